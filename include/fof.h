@@ -1,0 +1,214 @@
+/*
+ * fof.h -- C ABI of the GB300 Friends-of-Friends group finder.
+ *
+ * The library finds the Friends-of-Friends groups of float32 particle
+ * positions in a periodic cubic box: the connected components of the graph
+ * whose edges join particles at distance <= l_x (paper Sec. 1, footnote on
+ * the graph definition; "at most l_x", abstract).  Particles without a
+ * neighbour are groups of size one (Sec. 1).
+ *
+ * Method on the device (one GPU, sm_103a):
+ *   fof_link    counting-sort binning of the particles into cells of side
+ *               >= l_x (two-level: bricks, then cells inside each brick),
+ *               self- and neighbour-cell link kernels, and a lock-free
+ *               union-find forest in which the larger root is always hooked
+ *               onto the smaller one with an atomic compare-and-swap, with
+ *               path halving in Find (Sec. 2; Sec. 3.1; Sec. 3.2, CAS union;
+ *               Sec. 3.4.3, compression of deep paths only).
+ *   fof_groups  pointer-jumping finalisation of the forest, group sizes by
+ *               atomic counting with roots excluded (Sec. 3.4.1 and 3.4.2),
+ *               per-particle labels, the label-indexed size array and the
+ *               catalogue of groups of at least min_size members.
+ *
+ * Link predicate (the paper leaves the arithmetic open; this is the reading
+ * the library implements exactly): per axis d = (double)x_i - (double)x_j,
+ * wrapped once by "if d > L/2: d -= L; else if d < -L/2: d += L"; then
+ * s = (dx*dx + dy*dy) + dz*dz, each operation rounded to nearest in IEEE
+ * double, no fused multiply-add; linked iff s <= l_x*l_x (rounded once).
+ * The device evaluates this predicate exactly: a float32 pre-test with a
+ * proven error bound settles clear cases, every other pair takes the
+ * double-precision test above.
+ *
+ * Outputs (deterministic, independent of scheduling):
+ *   ids[i]    smallest particle index of i's group (union-by-root onto the
+ *             smaller offset makes the root the minimum, Sec. 2, Sec. 3.1);
+ *   sizes[g]  number of members of the group labelled g, 0 where g is not a
+ *             label (the paper's group_size indexed by the root, Sec. 3.4.1);
+ *   catalogue (label, size) of every group with size >= max(min_size, 1),
+ *             ascending label ("groups of length > 20", Sec. 4.1, is one
+ *             such threshold).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers (cudaMalloc, torch tensors on
+ *     the GPU); *_host are host pointers (pinned memory is fastest).  The
+ *     caller owns all of them.  Arrays are contiguous, int32 or float32,
+ *     positions are [n][3] float32 (x, y, z per particle, AoS).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Functions return FOF_OK (0) or a FOF_ERR_* code; fof_strerror() names
+ *     it.  No entry point throws, aborts or prints.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef FOF_GB300_H
+#define FOF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FOF_OK = 0,
+    FOF_ERR_ARG = 1,       /* invalid argument (see each function)          */
+    FOF_ERR_RANGE = 2,     /* a position is NaN, infinite or outside [0, L)  */
+    FOF_ERR_CAPACITY = 3,  /* catalogue larger than its capacity             */
+    FOF_ERR_STATE = 4,     /* fof_groups before fof_link, or similar order   */
+    FOF_ERR_OOM = 5,       /* device or pinned-host allocation failed        */
+    FOF_ERR_CUDA = 6,      /* a CUDA runtime call failed                     */
+    FOF_ERR_TIMEOUT = 7,   /* a bounded retry loop ran out (union CAS)       */
+    FOF_ERR_INTERNAL = 8   /* a device-side consistency check failed         */
+};
+
+typedef struct fof_plan *fof_handle;    /* opaque, owned by the library */
+
+typedef struct {
+    int32_t label;   /* smallest particle index of the group (box-local) */
+    int32_t size;    /* number of members                                */
+} fof_group;
+
+/* Tuning knobs; a zero field selects the library's default. */
+typedef struct {
+    int32_t cells_per_axis;  /* cells per box side; must keep side >= l_x   */
+    int32_t brick_cells;     /* cells per brick side: 1, 2, 4, 8 or 16      */
+    double occupancy;        /* target mean particles per cell (default 1.0) */
+    int32_t dense_min;       /* cell occupancy from which a warp links the
+                                cell cooperatively with root skipping        */
+    int32_t retry_cap;       /* max CAS attempts per union (default 2^20)    */
+    int32_t reserved[4];
+} fof_options;
+
+/* ---------------------------------------------------------------------- */
+/* single box                                                              */
+/* ---------------------------------------------------------------------- */
+
+/* Plan for one periodic box of side `box` with linking length `l_x` and `n`
+ * particles.  Allocates the device workspace (fof_workspace_bytes) and a
+ * small pinned host block.  Errors: FOF_ERR_ARG if box is not finite and
+ * > 0, l_x is not finite and > 0, l_x >= box/2, n < 0, n > 2^31 - 2, or out
+ * is NULL; FOF_ERR_OOM; FOF_ERR_CUDA. */
+int fof_create(double box, double l_x, int64_t n, fof_handle *out);
+
+/* As fof_create with options (may be NULL).  If `workspace_dev` is not
+ * NULL the plan uses that caller-owned device block of `workspace_bytes`
+ * (at least fof_workspace_bytes(...), 256-byte aligned) and allocates no
+ * device memory itself; the block must outlive the handle. */
+int fof_create_ex(double box, double l_x, int64_t n, const fof_options *opt,
+                  void *workspace_dev, size_t workspace_bytes, fof_handle *out);
+
+/* Device bytes a plan needs (0 if the arguments are invalid). */
+size_t fof_workspace_bytes(double box, double l_x, int64_t n, const fof_options *opt);
+
+/* ---------------------------------------------------------------------- */
+/* batch of independent boxes (the single box is the batch of one)         */
+/* ---------------------------------------------------------------------- */
+
+/* Plan for `nbox` boxes; box b has side box[b], linking length l_x[b] and
+ * n[b] particles (same rules as fof_create for each; total particles must
+ * stay <= 2^31 - 2).  Positions, ids and sizes of the boxes are
+ * concatenated in box order; ids and labels are local to their box. */
+int fof_batch_create(int32_t nbox, const double *box, const double *l_x,
+                     const int64_t *n, const fof_options *opt,
+                     void *workspace_dev, size_t workspace_bytes, fof_handle *out);
+
+size_t fof_batch_workspace_bytes(int32_t nbox, const double *box, const double *l_x,
+                                 const int64_t *n, const fof_options *opt);
+
+/* ---------------------------------------------------------------------- */
+/* running                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Enqueue binning and linking of pos_dev ([sum n][3] float32, device) on
+ * `stream`.  Asynchronous: returns once the kernels are enqueued; pos_dev
+ * must stay valid until they finish.  Out-of-range positions are reported
+ * by the next fof_groups (FOF_ERR_RANGE).  Errors: FOF_ERR_ARG (NULL
+ * handle, NULL pos_dev with n > 0), FOF_ERR_CUDA. */
+int fof_link(fof_handle h, const float *pos_dev, void *stream);
+
+/* Enqueue finalisation and outputs of the last fof_link, then wait for the
+ * stream and report.  ids_dev and sizes_dev hold sum(n) int32 each;
+ * catalogue_dev holds cat_capacity fof_group entries (may be NULL if
+ * cat_capacity is 0).  For a batch, the catalogue is concatenated in box
+ * order, min_size applies to every box, and n_groups_out / n_cat_out
+ * (host, may be NULL) receive one count per box.  If the catalogue has more
+ * than cat_capacity entries in total, the first cat_capacity are written,
+ * the counts are still reported and FOF_ERR_CAPACITY is returned.  Errors:
+ * FOF_ERR_STATE (no fof_link yet), FOF_ERR_RANGE, FOF_ERR_TIMEOUT,
+ * FOF_ERR_CAPACITY, FOF_ERR_ARG, FOF_ERR_CUDA. */
+int fof_groups(fof_handle h, int32_t *ids_dev, int32_t *sizes_dev,
+               fof_group *catalogue_dev, int64_t cat_capacity, int32_t min_size,
+               int64_t *n_groups_out, int64_t *n_cat_out, void *stream);
+
+/* fof_groups without the wait: counts and status stay on the device until
+ * fof_result().  Together with fof_link this sequence can be captured in a
+ * CUDA graph (it performs no host synchronisation and no allocation). */
+int fof_groups_async(fof_handle h, int32_t *ids_dev, int32_t *sizes_dev,
+                     fof_group *catalogue_dev, int64_t cat_capacity, int32_t min_size,
+                     void *stream);
+
+/* Wait for `stream` and report the status and counts of the last
+ * fof_groups_async (same meaning and errors as fof_groups). */
+int fof_result(fof_handle h, int64_t *n_groups_out, int64_t *n_cat_out, void *stream);
+
+/* Whole pipeline from HOST buffers: copies pos_host to the device, runs
+ * fof_link and fof_groups, and copies ids, sizes and the catalogue back
+ * into ids_host, sizes_host and catalogue_host.  Device staging buffers
+ * are allocated on the first call and kept by the handle.  Same errors as
+ * fof_groups, plus FOF_ERR_OOM. */
+int fof_run_host(fof_handle h, const float *pos_host, int32_t *ids_host, int32_t *sizes_host,
+                 fof_group *catalogue_host, int64_t cat_capacity, int32_t min_size,
+                 int64_t *n_groups_out, int64_t *n_cat_out, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* CUDA graph of the whole pipeline                                        */
+/* ---------------------------------------------------------------------- */
+
+/* Capture fof_link + fof_groups_async with these buffers into a graph kept
+ * by the handle (replacing any previous one).  `stream` must not be the
+ * legacy default stream. */
+int fof_graph_build(fof_handle h, const float *pos_dev, int32_t *ids_dev, int32_t *sizes_dev,
+                    fof_group *catalogue_dev, int64_t cat_capacity, int32_t min_size,
+                    void *stream);
+
+/* Launch the captured graph on `stream`; read results with fof_result. */
+int fof_graph_launch(fof_handle h, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* introspection                                                           */
+/* ---------------------------------------------------------------------- */
+
+/* Plan geometry of box b: cells per axis, cells per brick side, number of
+ * bricks per axis.  Any pointer may be NULL. */
+int fof_plan_info(fof_handle h, int32_t b, int32_t *cells_per_axis, int32_t *brick_cells,
+                  int32_t *bricks_per_axis);
+
+/* Per-phase device timing.  When enabled, every kernel phase is bracketed
+ * by CUDA events on the launching stream; fof_phase_times() then returns,
+ * for up to `max` phases, the summed milliseconds and launch counts since
+ * the last reset, and names[k] (static strings).  Returns the number of
+ * phases, or a negative FOF_ERR_* code. */
+int fof_set_timing(fof_handle h, int enable);
+int fof_phase_times(fof_handle h, double *ms, int64_t *launches, const char **names, int max);
+int fof_reset_times(fof_handle h);
+
+/* Number of kernel launches the handle has enqueued since creation. */
+int64_t fof_kernel_launches(fof_handle h);
+
+void fof_destroy(fof_handle h);
+const char *fof_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOF_GB300_H */

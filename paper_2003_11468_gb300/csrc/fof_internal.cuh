@@ -1,0 +1,294 @@
+// Internal declarations of the GB300 Friends-of-Friends library.
+//
+// Device building blocks shared by the kernels:
+//   * BoxDev: per-box geometry (a single box is a batch of one box);
+//   * cell index of a coordinate, in float32, with a proven margin;
+//   * the link predicate: a float32 pre-test whose error bound is derived in
+//     fof_plan.cu (setup_box), and the exact double-precision predicate for
+//     every pair the pre-test cannot settle;
+//   * the concurrent union-find: Find with path halving (writes only on
+//     paths of depth >= 2, paper Sec. 3.4.3) and Union by CAS hooking of the
+//     larger root onto the smaller one (Sec. 3.1, Sec. 3.2), retried while
+//     the hooked root changed under us, with a bounded retry count.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fofgpu {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// device error bits (combined into the status word with atomicOr)
+constexpr int kErrRange = 1;     // a coordinate outside [0, L) or not finite
+constexpr int kErrTimeout = 2;   // a union ran out of CAS retries
+constexpr int kErrInternal = 4;  // an internal consistency check failed
+constexpr int kFindCap = 1 << 26; // steps of one Find walk (a forest path is shorter)
+
+struct BoxDev {
+    int64_t p0;       // first particle of the box in the concatenated arrays
+    int64_t n;        // particles in the box
+    int64_t brick0;   // first brick of the box (concatenated brick arrays)
+    int64_t cell0;    // first cell of the box (concatenated cell arrays)
+    double L;         // box side
+    double l2;        // l_x * l_x rounded to double once
+    int32_t nb;       // bricks per axis
+    int32_t r;        // cells per brick per axis (power of two)
+    int32_t log2r;
+    int32_t nc;       // cells per axis = nb * r
+    float inv_h;      // float32(nc / L): cell index = min(nc-1, (int)(x * inv_h))
+    float Lf;         // float32(L) for the float32 pre-test
+    float xmax;       // largest float32 strictly below L (valid: 0 <= x <= xmax)
+    float t_lo;       // pre-test: d2f < t_lo  => linked
+    float t_hi;       // pre-test: d2f > t_hi  => not linked
+    int32_t pad;
+};
+
+// Per-run device status.
+struct Status {
+    int err;
+    int pad;
+    long long n_cat_total;
+};
+
+// ------------------------------------------------------------------------
+// box lookup: box index of a concatenated particle / brick index
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ int box_of(const int64_t* __restrict__ starts, int nbox, int64_t i)
+{
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {                 // last box with starts[b] <= i
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(starts + mid) <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------------
+// cells
+// ------------------------------------------------------------------------
+
+// Cell coordinate along one axis.  With cell side h = L/nc >= l_x (1 + 2^-9)
+// and nc <= 4096, the float32 rounding of x * inv_h moves a coordinate by at
+// most nc * 2^-23 < 2^-10 cells, so two coordinates that the exact predicate
+// links land in the same or in periodically adjacent cells.  Clamping keeps
+// every input (even an invalid one) inside the grid.
+__device__ __forceinline__ int cell_coord(float x, const BoxDev& b)
+{
+    int c = (int)__fmul_rn(x, b.inv_h);
+    c = c < 0 ? 0 : c;
+    return c > b.nc - 1 ? b.nc - 1 : c;
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v)   // 5 bits -> every 3rd bit
+{
+    v &= 0x1fu;
+    v = (v | (v << 8)) & 0x100fu;
+    v = (v | (v << 4)) & 0x10c3u;
+    v = (v | (v << 2)) & 0x1249u;
+    return v;
+}
+
+// Morton order of a cell inside its brick (r <= 32).
+__device__ __forceinline__ uint32_t local_code(int lx, int ly, int lz)
+{
+    return spread3((uint32_t)lx) | (spread3((uint32_t)ly) << 1) | (spread3((uint32_t)lz) << 2);
+}
+
+__device__ __forceinline__ int64_t brick_local(const BoxDev& b, int cx, int cy, int cz)
+{
+    int s = b.log2r;
+    return ((int64_t)(cz >> s) * b.nb + (cy >> s)) * b.nb + (cx >> s);
+}
+
+// Concatenated cell index: cells are ordered brick by brick (row-major
+// bricks), Morton order inside a brick.
+__device__ __forceinline__ int64_t cell_key(const BoxDev& b, int cx, int cy, int cz)
+{
+    int m = b.r - 1;
+    int64_t r3 = (int64_t)b.r * b.r * b.r;
+    return b.cell0 + brick_local(b, cx, cy, cz) * r3 + local_code(cx & m, cy & m, cz & m);
+}
+
+__device__ __forceinline__ int wrap_cell(int c, int nc)
+{
+    return c < 0 ? c + nc : (c >= nc ? c - nc : c);
+}
+
+// The 13 forward neighbours of the half stencil: dz > 0, or dz == 0 and
+// dy > 0, or dz == dy == 0 and dx > 0.  Offsets packed as (dx+1) + 3(dy+1)
+// + 9(dz+1).
+__device__ __forceinline__ void fwd_offset(int k, int& dx, int& dy, int& dz)
+{
+    // k = 0..12
+    int code = k < 9 ? 18 + k : (k < 12 ? 15 + (k - 9) : 14);
+    dx = code % 3 - 1;
+    dy = (code / 3) % 3 - 1;
+    dz = code / 9 - 1;
+}
+
+// ------------------------------------------------------------------------
+// the link predicate
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ float sep_f32(float a, float b, float Lf)
+{
+    float d = fabsf(__fsub_rn(a, b));
+    return fminf(d, __fsub_rn(Lf, d));
+}
+
+__device__ __forceinline__ float d2_f32(const float4& p, const float4& q, float Lf)
+{
+    float mx = sep_f32(p.x, q.x, Lf);
+    float my = sep_f32(p.y, q.y, Lf);
+    float mz = sep_f32(p.z, q.z, Lf);
+    return __fmaf_rn(mz, mz, __fmaf_rn(my, my, __fmul_rn(mx, mx)));
+}
+
+__device__ __forceinline__ double wrap64(double d, double L)
+{
+    double half = 0.5 * L;
+    if (d > half)
+        d = __dsub_rn(d, L);
+    else if (d < -half)
+        d = __dadd_rn(d, L);
+    return d;
+}
+
+// Exact predicate: s = (dx*dx + dy*dy) + dz*dz in IEEE double with every
+// operation rounded to nearest and no contraction; linked iff s <= l2.
+static __device__ __noinline__ bool linked_exact(float4 p, float4 q, double L, double l2)
+{
+    double dx = wrap64(__dsub_rn((double)p.x, (double)q.x), L);
+    double dy = wrap64(__dsub_rn((double)p.y, (double)q.y), L);
+    double dz = wrap64(__dsub_rn((double)p.z, (double)q.z), L);
+    double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    s = __dadd_rn(s, __dmul_rn(dz, dz));
+    return s <= l2;
+}
+
+// Pre-test in float32, exact test only inside the uncertainty band.
+__device__ __forceinline__ bool linked(const float4& p, const float4& q, const BoxDev& b)
+{
+    float s = d2_f32(p, q, b.Lf);
+    if (s > b.t_hi)
+        return false;
+    if (s < b.t_lo)
+        return true;
+    return linked_exact(p, q, b.L, b.l2);
+}
+
+// ------------------------------------------------------------------------
+// union-find on the parent array (indices into the binned particle order)
+// ------------------------------------------------------------------------
+
+// Loads and stores at gpu scope, served by L2, so that a retry after a
+// failed CAS sees the other SMs' hooks (L1 is not coherent).
+__device__ __forceinline__ int ld_relaxed(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(int* p, int v)
+{
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Find with path halving.  Every value parent[x] ever holds is an ancestor
+// of x (hooks only change roots, halving only skips to a grandparent), so
+// racing writes are harmless; the walk strictly decreases x and ends.  The
+// step cap only guards against a corrupted forest (it reports, never hangs).
+__device__ __forceinline__ int uf_find(int* parent, int x, int* err)
+{
+    int p = ld_relaxed(parent + x);
+    for (int step = 0; p != x; ++step) {
+        int gp = ld_relaxed(parent + p);
+        if (gp == p)
+            return p;
+        if (step >= kFindCap || gp > p) {
+            atomicOr(err, kErrInternal);
+            return p;
+        }
+        st_relaxed(parent + x, gp);
+        x = gp;
+        p = ld_relaxed(parent + x);
+    }
+    return x;
+}
+
+// Union by root: hook the larger root onto the smaller with CAS, which only
+// succeeds while the larger is still a root; otherwise re-find and retry.
+// Keeps parent[x] <= x, hence no cycles.  Returns the root reached.
+__device__ __forceinline__ int uf_union(int* parent, int a, int b, int cap, int* err)
+{
+    for (int it = 0; it < cap; ++it) {
+        a = uf_find(parent, a, err);
+        b = uf_find(parent, b, err);
+        if (a == b)
+            return a;
+        int hi = a > b ? a : b;
+        int lo = a > b ? b : a;
+        if (atomicCAS(parent + hi, hi, lo) == hi)
+            return lo;
+    }
+    atomicOr(err, kErrTimeout);
+    return a < b ? a : b;
+}
+
+// ------------------------------------------------------------------------
+// kernel launchers (one per phase); each returns cudaGetLastError()
+// ------------------------------------------------------------------------
+
+struct Geometry {
+    const BoxDev* boxes;       // [nbox]
+    const int64_t* box_p0;     // [nbox] first particle of each box
+    const int64_t* box_brick0; // [nbox] first brick of each box
+    int nbox;
+    int64_t total_n;           // particles over all boxes
+    int64_t total_bricks;
+    int64_t total_cells;
+};
+
+struct Work {
+    float4* tmp;        // [total_n] particles in brick order
+    float4* sorted;     // [total_n] particles in cell order, w = box-local index
+    int* parent;        // [total_n] union-find forest over cell-order slots
+    int* minorig;       // [total_n] smallest box-local index per root
+    int* cnt;           // [total_n] group size per root
+    int* cell_start;    // [total_cells + 1]
+    int* bcount;        // [total_bricks + 1]
+    int* bstart;        // [total_bricks + 1]
+    int* bcursor;       // [total_bricks]
+    int* scan_tmp;      // scan partials
+    int64_t scan_tmp_len;
+    int* tile_cnt;      // [n_tiles + 1] catalogue entries per label tile
+    int* tile_off;      // [n_tiles + 1]
+    int64_t n_tiles;
+    Status* status;     // device status
+    unsigned long long* n_groups;  // [nbox]
+    unsigned long long* n_cat;     // [nbox]
+};
+
+constexpr int kCatTile = 2048;  // labels per catalogue tile
+
+int sm_count();
+
+cudaError_t launch_bin_count(const float* pos, const Geometry& g, const Work& w, cudaStream_t s);
+cudaError_t launch_scan(const int* in, int* out, int64_t len, int* tmp, int64_t tmp_len,
+                        cudaStream_t s);
+int64_t scan_tmp_elems(int64_t len);
+cudaError_t launch_bin_scatter(const float* pos, const Geometry& g, const Work& w, cudaStream_t s);
+cudaError_t launch_brick_sort(const Geometry& g, const Work& w, cudaStream_t s);
+cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, int retry_cap,
+                        cudaStream_t s);
+cudaError_t launch_finalize(const Geometry& g, const Work& w, cudaStream_t s);
+cudaError_t launch_outputs(const Geometry& g, const Work& w, int32_t* ids, int32_t* sizes,
+                           int32_t min_size, cudaStream_t s);
+cudaError_t launch_catalogue(const Geometry& g, const Work& w, const int32_t* sizes,
+                             int32_t min_size, int2* cat, int64_t cap, cudaStream_t s);
+
+}  // namespace fofgpu

@@ -1,0 +1,189 @@
+// Self- and pair-cell linking (the paper's "self" and "pair" tasks over
+// cells, Sec. 3.1, Fig. 1), on the binned particle order.
+//
+// A warp takes 32 consecutive binned particles (one per lane).  For every
+// particle the cell itself and its 13 forward neighbours (half of the
+// periodic 26-neighbourhood) are searched, so each unordered cell pair is
+// visited once; inside the own cell only partners with a larger slot are
+// tested.
+//
+// Dense cells (at least `dense_min` particles) are linked by the warp as a
+// team: the lanes that belong to the cell keep their current root, the
+// candidates of a neighbour cell are loaded 32 at a time (coalesced float4)
+// with a snapshot of their roots, and
+//   * a chunk is skipped when all roots on both sides already agree,
+//   * a single candidate is skipped when every lane's root equals its root,
+// which is exact because groups only ever merge: two particles whose roots
+// were once equal stay in one group.  Sparse particles search on their own.
+//
+// Linked pairs are merged with the CAS union of fof_internal.cuh.
+#include "fof_internal.cuh"
+
+namespace fofgpu {
+
+namespace {
+
+struct Cell {
+    int cx, cy, cz;
+};
+
+__device__ __forceinline__ int64_t nbr_key(const BoxDev& b, const Cell& c, int k)
+{
+    int dx, dy, dz;
+    fwd_offset(k, dx, dy, dz);
+    return cell_key(b, wrap_cell(c.cx + dx, b.nc), wrap_cell(c.cy + dy, b.nc),
+                    wrap_cell(c.cz + dz, b.nc));
+}
+
+// Neighbour k duplicates the own cell or an earlier neighbour (only when
+// fewer than 3 cells per axis).
+__device__ __forceinline__ bool nbr_duplicate(const BoxDev& b, const Cell& c, int k, int64_t self)
+{
+    if (b.nc >= 3)
+        return false;
+    int64_t key = nbr_key(b, c, k);
+    if (key == self)
+        return true;
+    for (int q = 0; q < k; ++q)
+        if (nbr_key(b, c, q) == key)
+            return true;
+    return false;
+}
+
+__device__ __forceinline__ float4 shfl4(float4 v, int src)
+{
+    v.x = __shfl_sync(kFull, v.x, src);
+    v.y = __shfl_sync(kFull, v.y, src);
+    v.z = __shfl_sync(kFull, v.z, src);
+    return v;
+}
+
+// One warp links the lanes in `peers` (all in cell `self` of box b) against
+// the candidates in [j0, j1).  `own` = the candidates lie in the own cell,
+// so lane i only takes j > its slot.
+__device__ __forceinline__ void team_link(int* __restrict__ parent, const float4* __restrict__ sorted,
+                                          const BoxDev& b, bool mine, int64_t s, const float4& p,
+                                          int& ri, int j0, int j1, bool own, int cap, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    for (int jb = j0; jb < j1; jb += kWarp) {
+        int j = jb + lane;
+        bool jv = j < j1;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        int rj = -1;
+        if (jv) {
+            q = sorted[j];
+            rj = uf_find(parent, j, err);
+        }
+        // chunk skip: every root on both sides equal to one value
+        int ref = __shfl_sync(kFull, mine ? ri : rj, __ffs(__ballot_sync(kFull, mine)) - 1);
+        bool agree = (!mine || ri == ref) && (!jv || rj == ref);
+        if (__all_sync(kFull, agree))
+            continue;
+        int kmax = j1 - jb < kWarp ? j1 - jb : kWarp;
+        for (int t = 0; t < kmax; ++t) {
+            int rt = __shfl_sync(kFull, rj, t);
+            float4 qt = shfl4(q, t);
+            bool need = mine && ri != rt && (!own || jb + t > s);
+            if (!__any_sync(kFull, need))
+                continue;
+            if (need && linked(p, qt, b))
+                ri = uf_union(parent, ri, rt, cap, err);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restrict__ sorted,
+                                              const int* __restrict__ cell_start, int* parent,
+                                              int dense_min, int cap, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+
+    for (int64_t base = warp * kWarp; base < g.total_n; base += nwarps * kWarp) {
+        const int64_t s = base + lane;
+        const bool valid = s < g.total_n;
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        int bi = 0;
+        Cell c{0, 0, 0};
+        int64_t self = -1;
+        int c0 = 0, c1 = 0;
+        if (valid) {
+            p = sorted[s];
+            bi = box_of(g.box_p0, g.nbox, s);
+            const BoxDev& b = g.boxes[bi];
+            c.cx = cell_coord(p.x, b);
+            c.cy = cell_coord(p.y, b);
+            c.cz = cell_coord(p.z, b);
+            self = cell_key(b, c.cx, c.cy, c.cz);
+            c0 = cell_start[self];
+            c1 = cell_start[self + 1];
+        }
+        const bool dense = valid && (c1 - c0) >= dense_min;
+        unsigned dmask = __ballot_sync(kFull, dense);
+
+        // ---- dense cells: the whole warp links each cell as a team ----
+        while (dmask) {
+            const int lead = __ffs(dmask) - 1;
+            const int64_t key = __shfl_sync(kFull, self, lead);
+            const bool mine = dense && self == key;
+            const unsigned peers = __ballot_sync(kFull, mine);
+            dmask &= ~peers;
+            const int tbi = __shfl_sync(kFull, bi, lead);
+            const BoxDev& b = g.boxes[tbi];
+            Cell tc;
+            tc.cx = __shfl_sync(kFull, c.cx, lead);
+            tc.cy = __shfl_sync(kFull, c.cy, lead);
+            tc.cz = __shfl_sync(kFull, c.cz, lead);
+            int ri = mine ? uf_find(parent, (int)s, err) : -1;
+            // own cell: partners after the first lane of the team
+            {
+                int first = (int)__shfl_sync(kFull, s, lead);
+                int end = __shfl_sync(kFull, c1, lead);
+                team_link(parent, sorted, b, mine, s, p, ri, first + 1, end, true, cap, err);
+            }
+            for (int k = 0; k < 13; ++k) {
+                if (nbr_duplicate(b, tc, k, key))
+                    continue;
+                int64_t nk = nbr_key(b, tc, k);
+                int j0 = cell_start[nk], j1 = cell_start[nk + 1];
+                team_link(parent, sorted, b, mine, s, p, ri, j0, j1, false, cap, err);
+            }
+        }
+
+        // ---- sparse cells: every lane on its own ----
+        if (valid && !dense) {
+            const BoxDev& b = g.boxes[bi];
+            for (int j = (int)s + 1; j < c1; ++j)
+                if (linked(p, sorted[j], b))
+                    uf_union(parent, (int)s, j, cap, err);
+            for (int k = 0; k < 13; ++k) {
+                if (nbr_duplicate(b, c, k, self))
+                    continue;
+                int64_t nk = nbr_key(b, c, k);
+                int j0 = cell_start[nk], j1 = cell_start[nk + 1];
+                for (int j = j0; j < j1; ++j)
+                    if (linked(p, sorted[j], b))
+                        uf_union(parent, (int)s, j, cap, err);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, int retry_cap, cudaStream_t s)
+{
+    if (g.total_n == 0)
+        return cudaSuccess;
+    int64_t warps = (g.total_n + kWarp - 1) / kWarp;
+    int64_t blocks = (warps * kWarp + 255) / 256;
+    int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    k_link<<<(unsigned)blocks, 256, 0, s>>>(g, w.sorted, w.cell_start, w.parent, dense_min, retry_cap,
+                                            &w.status->err);
+    return cudaGetLastError();
+}
+
+}  // namespace fofgpu

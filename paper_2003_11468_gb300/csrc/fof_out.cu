@@ -1,0 +1,216 @@
+// Flattening the forest into outputs.
+//
+//   finalize   full pointer jumping: parent[s] = root(s) for every slot; each
+//              non-root adds itself to its root's size and offers its input
+//              index to the root's minimum.  Roots were initialised with
+//              size 1 and their own index, so they take part in no atomic:
+//              the paper's early elimination of singletons (Sec. 3.4.2),
+//              with the atomic additions of its parallel size count
+//              (Sec. 3.4.1) aggregated per warp.
+//   outputs    ids[i] = smallest index of i's group; sizes[label] = size,
+//              0 elsewhere; per-box group counts; catalogue entries counted
+//              per label tile.
+//   catalogue  prefix sum over the label tiles, then each tile writes its
+//              (label, size) entries in ascending label order.
+#include "fof_internal.cuh"
+
+namespace fofgpu {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_finalize(int64_t total, int* __restrict__ parent,
+                                                  int* __restrict__ minorig, int* __restrict__ cnt,
+                                                  int* __restrict__ err)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
+        int64_t s = base + threadIdx.x;
+        bool valid = s < total;
+        unsigned active = __ballot_sync(kFull, valid);
+        if (!valid)
+            continue;
+        int p = parent[s];
+        int root = (int)s;
+        if (p != (int)s) {
+            int x = p;
+            int q = parent[x];
+            for (int step = 0; q != x; ++step) {
+                if (q > x || step >= kFindCap) {   // corrupted forest: report
+                    atomicOr(err, kErrInternal);
+                    break;
+                }
+                x = q;
+                q = parent[x];
+            }
+            root = x;
+            if (p != root)
+                parent[s] = root;
+        }
+        bool nonroot = root != (int)s;
+        unsigned nr = __ballot_sync(active, nonroot);
+        if (!nonroot)
+            continue;
+        unsigned peers = __match_any_sync(nr, root);
+        int leader = __ffs(peers) - 1;
+        unsigned mn = __reduce_min_sync(peers, (unsigned)minorig[s]);
+        if ((threadIdx.x & 31) == leader) {
+            atomicAdd(cnt + root, __popc(peers));
+            atomicMin(minorig + root, (int)mn);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_outputs(Geometry g, const float4* __restrict__ sorted,
+                                                 const int* __restrict__ parent,
+                                                 const int* __restrict__ minorig,
+                                                 const int* __restrict__ cnt,
+                                                 int32_t* __restrict__ ids, int32_t* __restrict__ sizes,
+                                                 int32_t thr, unsigned long long* __restrict__ n_groups,
+                                                 unsigned long long* __restrict__ n_cat,
+                                                 int* __restrict__ tile_cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.total_n; base += stride) {
+        int64_t s = base + threadIdx.x;
+        bool valid = s < g.total_n;
+        unsigned active = __ballot_sync(kFull, valid);
+        if (!valid)
+            continue;
+        int bi = box_of(g.box_p0, g.nbox, s);
+        int64_t p0 = g.boxes[bi].p0;
+        int root = parent[s];
+        int label = minorig[root];
+        int size = cnt[root];
+        int o = __float_as_int(sorted[s].w);
+        ids[p0 + o] = label;
+        sizes[p0 + o] = (o == label) ? size : 0;
+        bool is_root = root == (int)s;
+        bool in_cat = is_root && size >= thr;
+        // per-box counts, aggregated over lanes of the same box
+        unsigned peers = __match_any_sync(active, bi);
+        int leader = __ffs(peers) - 1;
+        int ng = __popc(__ballot_sync(active, is_root) & peers);
+        int nk = __popc(__ballot_sync(active, in_cat) & peers);
+        if (lane == leader) {
+            if (ng) atomicAdd(n_groups + bi, (unsigned long long)ng);
+            if (nk) atomicAdd(n_cat + bi, (unsigned long long)nk);
+        }
+        if (in_cat)
+            atomicAdd(tile_cnt + (p0 + label) / kCatTile, 1);
+    }
+}
+
+constexpr int kCatThreads = 256;
+constexpr int kCatItems = kCatTile / kCatThreads;   // 8
+
+__device__ __forceinline__ int block_excl(int v, int* sw, int& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int t = lane < nw ? sw[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) sw[lane] = t;
+    }
+    __syncthreads();
+    int off = wid ? sw[wid - 1] : 0;
+    total = sw[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return off + x - v;
+}
+
+// One block per tile of kCatTile labels: entries of the tile in ascending
+// label order at tile_off[tile].
+__global__ void __launch_bounds__(kCatThreads) k_catalogue(Geometry g, const int32_t* __restrict__ sizes,
+                                                           const int* __restrict__ tile_cnt,
+                                                           const int* __restrict__ tile_off,
+                                                           int32_t thr, int2* __restrict__ cat,
+                                                           int64_t cap, Status* status)
+{
+    __shared__ int sw[32];
+    for (int64_t tile = blockIdx.x; tile * kCatTile < g.total_n; tile += gridDim.x) {
+        if (tile_cnt[tile] == 0)
+            continue;      // block-uniform
+        int64_t base = tile * kCatTile + (int64_t)threadIdx.x * kCatItems;
+        int v[kCatItems];
+        int f = 0;
+        for (int k = 0; k < kCatItems; ++k) {
+            int64_t i = base + k;
+            v[k] = i < g.total_n ? sizes[i] : 0;
+            f += v[k] >= thr;
+        }
+        int total;
+        int64_t off = tile_off[tile] + block_excl(f, sw, total);
+        for (int k = 0; k < kCatItems; ++k) {
+            if (v[k] >= thr) {
+                int64_t i = base + k;
+                if (off < cap) {
+                    int bi = box_of(g.box_p0, g.nbox, i);
+                    cat[off] = make_int2((int)(i - g.boxes[bi].p0), v[k]);
+                }
+                ++off;
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int64_t nt = (g.total_n + kCatTile - 1) / kCatTile;
+        status->n_cat_total = tile_off[nt];
+    }
+}
+
+}  // namespace
+
+static int grid_for(int64_t items, int threads, int per_sm)
+{
+    int64_t want = (items + threads - 1) / threads;
+    int64_t cap = (int64_t)sm_count() * per_sm;
+    if (want < 1) want = 1;
+    return (int)(want < cap ? want : cap);
+}
+
+cudaError_t launch_finalize(const Geometry& g, const Work& w, cudaStream_t s)
+{
+    if (g.total_n == 0)
+        return cudaSuccess;
+    k_finalize<<<grid_for(g.total_n, 256, 8), 256, 0, s>>>(g.total_n, w.parent, w.minorig, w.cnt,
+                                                          &w.status->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outputs(const Geometry& g, const Work& w, int32_t* ids, int32_t* sizes,
+                           int32_t min_size, cudaStream_t s)
+{
+    if (g.total_n == 0)
+        return cudaSuccess;
+    int32_t thr = min_size < 1 ? 1 : min_size;
+    k_outputs<<<grid_for(g.total_n, 256, 8), 256, 0, s>>>(g, w.sorted, w.parent, w.minorig, w.cnt, ids,
+                                                        sizes, thr, w.n_groups, w.n_cat, w.tile_cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_catalogue(const Geometry& g, const Work& w, const int32_t* sizes, int32_t min_size,
+                             int2* cat, int64_t cap, cudaStream_t s)
+{
+    if (g.total_n == 0)
+        return cudaSuccess;
+    int32_t thr = min_size < 1 ? 1 : min_size;
+    cudaError_t e = launch_scan(w.tile_cnt, w.tile_off, w.n_tiles, w.scan_tmp, w.scan_tmp_len, s);
+    if (e != cudaSuccess)
+        return e;
+    int blocks = grid_for(w.n_tiles * kCatThreads, kCatThreads, 8);
+    k_catalogue<<<blocks, kCatThreads, 0, s>>>(g, sizes, w.tile_cnt, w.tile_off, thr, cat, cap, w.status);
+    return cudaGetLastError();
+}
+
+}  // namespace fofgpu

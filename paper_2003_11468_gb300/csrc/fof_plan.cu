@@ -1,0 +1,781 @@
+// Plan, workspace and C ABI of the Friends-of-Friends library (fof.h).
+//
+// A plan holds the geometry of one or more independent periodic boxes, a
+// device workspace sized for them, and a small pinned host block for the
+// status read-back.  fof_link enqueues binning and linking; fof_groups
+// enqueues finalisation and outputs and reads the status back once.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fof.h"
+#include "fof_internal.cuh"
+
+using namespace fofgpu;
+
+namespace fofgpu {
+
+int sm_count()
+{
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            cached = v;
+        else
+            return 152;
+    }
+    return cached;
+}
+
+}  // namespace fofgpu
+
+namespace {
+
+enum Phase {
+    kPhBinCount, kPhScanBricks, kPhBinScatter, kPhBrickSort, kPhLink,
+    kPhFinalize, kPhOutputs, kPhCatalogue, kNumPhases
+};
+
+const char* kPhaseNames[kNumPhases] = {
+    "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "link",
+    "finalize", "outputs", "catalogue",
+};
+const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 1, 1, 1, 4};
+
+constexpr int64_t kMaxTotal = 2147483646LL;   // slots and labels are int32
+constexpr int kDefaultRetryCap = 1 << 20;
+constexpr int kDefaultDenseMin = 24;
+constexpr int kMaxCellsPerAxis = 4096;        // float32 cell-index precision
+
+// Results block (device and pinned host copy): status, then per-box counts.
+struct ResultsLayout {
+    size_t status_off, groups_off, cat_off, bytes;
+};
+
+ResultsLayout results_layout(int nbox)
+{
+    ResultsLayout r;
+    r.status_off = 0;
+    r.groups_off = 64;
+    r.cat_off = r.groups_off + sizeof(long long) * (size_t)nbox;
+    r.bytes = r.cat_off + sizeof(long long) * (size_t)nbox;
+    return r;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+float float_up(double v)        // smallest float >= v
+{
+    float f = (float)v;
+    while ((double)f < v) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+float float_down(double v)      // largest float <= v
+{
+    float f = (float)v;
+    while ((double)f > v) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+// Geometry and predicate constants of one box.
+//
+// Cell size.  Cells per axis nc <= floor(L / (l_x (1 + 2^-9))) and
+// nc <= 4096, so the cell side h = L/nc >= l_x (1 + 2^-9).  The device
+// computes a cell coordinate as (int)fl32(x * fl32(nc/L)); two roundings of
+// relative size 2^-24 shift a coordinate by at most nc 2^-23 <= 2^-11 cell,
+// and two coordinates by at most 2^-10 cell.  A pair that the exact
+// predicate links is at most l_x (1 + 2^-50) apart per axis, i.e. less
+// than 1 - 2^-9 + 2^-18 cells, so its computed cells differ by at most one
+// (periodically).  Hence the 27-cell stencil finds every linked pair.
+//
+// Float32 pre-test.  For coordinates a, b in [0, L) the device computes per
+// axis m = min(|fl(a - b)|, fl(fl32(L) - |fl(a - b)|)).  With u = 2^-24,
+// |m - t| <= E1 = 3.01 u L where t = min(|a - b|, L - |a - b|) is the exact
+// periodic separation (one rounding of the difference, one of L, one of the
+// second difference).  The sum sf = fma(mz,mz, fma(my,my, mx*mx)) is within
+// a factor (1 +- 3.01 u) of |m|^2.  The exact double predicate deviates from
+// |t| by at most 2^-51 L per axis (roundings of the difference and of the
+// wrap) and compares against l2 = l_x^2 (1 +- 2^-53).  Therefore, with
+// E = E1 + 2^-51 L and sqrt(3) < 1.733:
+//   linked exactly  =>  sf <= (l_x (1 + 2^-50) + 1.733 E)^2 (1 + 3.01 u)
+//   sf < (l_x (1 - 2^-50) - 1.733 E)^2 (1 - 3.01 u)  =>  linked exactly.
+// Both bounds get a further relative slack of 2^-20 and are rounded outward
+// to float32.  Pairs between them take the exact double test.
+int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
+{
+    if (!std::isfinite(L) || !(L > 0.0) || !std::isfinite(l_x) || !(l_x > 0.0) ||
+        !(l_x < 0.5 * L) || n < 0 || n > kMaxTotal || L > 1e30)
+        return FOF_ERR_ARG;
+    std::memset(&b, 0, sizeof(b));
+    double q = std::floor(L / (l_x * (1.0 + std::ldexp(1.0, -9))));
+    int64_t nc_max = q < 1.0 ? 1 : (q > kMaxCellsPerAxis ? kMaxCellsPerAxis : (int64_t)q);
+    int64_t nc;
+    if (o && o->cells_per_axis > 0) {
+        if (o->cells_per_axis > nc_max)
+            return FOF_ERR_ARG;
+        nc = o->cells_per_axis;
+    } else {
+        double occ = (o && o->occupancy > 0.0) ? o->occupancy : 1.0;
+        double t = std::floor(std::cbrt((double)n / occ));
+        nc = t < 1.0 ? 1 : (int64_t)t;
+        if (nc > nc_max) nc = nc_max;
+    }
+    int r;
+    if (o && o->brick_cells > 0) {
+        r = o->brick_cells;
+        if ((r & (r - 1)) != 0 || r > 16 || r > nc)
+            return FOF_ERR_ARG;
+    } else {
+        r = nc >= 128 ? 16 : (nc >= 32 ? 8 : (nc >= 8 ? 4 : (nc >= 4 ? 2 : 1)));
+    }
+    int log2r = 0;
+    while ((1 << log2r) < r) ++log2r;
+    int64_t nb = nc / r;
+    nc = nb * r;
+
+    b.n = n;
+    b.L = L;
+    b.l2 = l_x * l_x;
+    b.nb = (int32_t)nb;
+    b.r = r;
+    b.log2r = log2r;
+    b.nc = (int32_t)nc;
+    b.inv_h = (float)((double)nc / L);
+    b.Lf = (float)L;
+    b.xmax = (float)L;
+    while ((double)b.xmax >= L) b.xmax = std::nextafter(b.xmax, 0.0f);
+
+    const double u = std::ldexp(1.0, -24);
+    const double E = 3.01 * u * L + std::ldexp(L, -51);
+    const double slack = std::ldexp(1.0, -20);
+    double rhi = l_x * (1.0 + std::ldexp(1.0, -50)) + 1.733 * E;
+    double thi = rhi * rhi * (1.0 + 3.01 * u) * (1.0 + slack);
+    double rlo = l_x * (1.0 - std::ldexp(1.0, -50)) - 1.733 * E;
+    double tlo = rlo > 0.0 ? rlo * rlo * (1.0 - 3.01 * u) * (1.0 - slack) : 0.0;
+    b.t_hi = float_up(thi);
+    b.t_lo = tlo > 0.0 ? float_down(tlo) : 0.0f;
+    return FOF_OK;
+}
+
+struct PhaseTimer {
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool pending = false;
+    double ms = 0.0;
+    int64_t launches = 0;
+};
+
+}  // namespace
+
+struct fof_plan {
+    int nbox = 0;
+    std::vector<BoxDev> boxes;
+    std::vector<int64_t> p0, brick0;
+    Geometry g{};
+    Work w{};
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    char* results_dev = nullptr;
+    char* results_host = nullptr;   // pinned
+    ResultsLayout rl{};
+    int dense_min = kDefaultDenseMin;
+    int retry_cap = kDefaultRetryCap;
+    bool linked = false;
+    bool pending = false;
+    int64_t last_cap = 0;
+    bool timing = false;
+    bool capturing = false;
+    PhaseTimer phase[kNumPhases];
+    int64_t launches = 0;
+    // fof_run_host staging
+    float* pos_d = nullptr;
+    int32_t* ids_d = nullptr;
+    int32_t* sizes_d = nullptr;
+    int2* cat_d = nullptr;
+    int64_t cat_d_cap = 0;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_cap = 0;
+};
+
+namespace {
+
+struct Layout {
+    size_t boxes, p0, brick0, results, bcount, bstart, bcursor, scan_tmp, tile_cnt, tile_off,
+        cell_start, tmp, sorted, parent, minorig, cnt, total;
+    int64_t scan_len, n_tiles;
+};
+
+Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cells)
+{
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + (bytes ? bytes : 1), 256);
+        return at;
+    };
+    L.n_tiles = (total_n + kCatTile - 1) / kCatTile;
+    int64_t s1 = scan_tmp_elems(total_bricks), s2 = scan_tmp_elems(L.n_tiles);
+    L.scan_len = s1 > s2 ? s1 : s2;
+    L.boxes = take(sizeof(BoxDev) * (size_t)nbox);
+    L.p0 = take(8 * (size_t)nbox);
+    L.brick0 = take(8 * (size_t)nbox);
+    L.results = take(results_layout(nbox).bytes);
+    L.bcount = take(4 * (size_t)(total_bricks + 1));
+    L.bstart = take(4 * (size_t)(total_bricks + 1));
+    L.bcursor = take(4 * (size_t)(total_bricks + 1));
+    L.scan_tmp = take(4 * (size_t)L.scan_len);
+    L.tile_cnt = take(4 * (size_t)(L.n_tiles + 1));
+    L.tile_off = take(4 * (size_t)(L.n_tiles + 1));
+    L.cell_start = take(4 * (size_t)(total_cells + 1));
+    L.tmp = take(16 * (size_t)total_n);
+    L.sorted = take(16 * (size_t)total_n);
+    L.parent = take(4 * (size_t)total_n);
+    L.minorig = take(4 * (size_t)total_n);
+    L.cnt = take(4 * (size_t)total_n);
+    L.total = off;
+    return L;
+}
+
+int setup_batch(int32_t nbox, const double* box, const double* l_x, const int64_t* n,
+                const fof_options* opt, std::vector<BoxDev>& boxes, int64_t& tn, int64_t& tb,
+                int64_t& tc)
+{
+    if (nbox < 1 || !box || !l_x || !n)
+        return FOF_ERR_ARG;
+    boxes.resize(nbox);
+    tn = tb = tc = 0;
+    for (int i = 0; i < nbox; ++i) {
+        int rc = setup_box(box[i], l_x[i], n[i], opt, boxes[i]);
+        if (rc != FOF_OK)
+            return rc;
+        BoxDev& b = boxes[i];
+        b.p0 = tn;
+        b.brick0 = tb;
+        b.cell0 = tc;
+        int64_t nb3 = (int64_t)b.nb * b.nb * b.nb;
+        tn += b.n;
+        tb += nb3;
+        tc += nb3 * (int64_t)b.r * b.r * b.r;
+        if (tn > kMaxTotal)
+            return FOF_ERR_ARG;
+    }
+    return FOF_OK;
+}
+
+int cuda_rc(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return FOF_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return FOF_ERR_OOM;
+    return FOF_ERR_CUDA;
+}
+
+#define FOF_TRY(expr)                                  \
+    do {                                               \
+        cudaError_t e_ = (expr);                       \
+        if (e_ != cudaSuccess) return cuda_rc(e_);     \
+    } while (0)
+
+void phase_begin(fof_plan* h, int ph, cudaStream_t s)
+{
+    h->launches += kPhaseLaunches[ph];
+    h->phase[ph].launches += kPhaseLaunches[ph];
+    if (h->timing && !h->capturing) {
+        cudaEventRecord(h->phase[ph].ev0, s);
+    }
+}
+
+void phase_end(fof_plan* h, int ph, cudaStream_t s)
+{
+    if (h->timing && !h->capturing) {
+        cudaEventRecord(h->phase[ph].ev1, s);
+        h->phase[ph].pending = true;
+    }
+}
+
+void collect_times(fof_plan* h)
+{
+    for (int k = 0; k < kNumPhases; ++k) {
+        PhaseTimer& t = h->phase[k];
+        if (!t.pending)
+            continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.ev0, t.ev1) == cudaSuccess)
+            t.ms += ms;
+        t.pending = false;
+    }
+}
+
+int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_t* n,
+                const fof_options* opt, void* workspace, size_t workspace_bytes, fof_handle* out)
+{
+    if (!out)
+        return FOF_ERR_ARG;
+    *out = nullptr;
+    std::vector<BoxDev> boxes;
+    int64_t tn, tb, tc;
+    int rc = setup_batch(nbox, box, l_x, n, opt, boxes, tn, tb, tc);
+    if (rc != FOF_OK)
+        return rc;
+    Layout L = layout(nbox, tn, tb, tc);
+    if (workspace && (workspace_bytes < L.total || ((uintptr_t)workspace & 255u)))
+        return FOF_ERR_ARG;
+
+    fof_plan* h = new (std::nothrow) fof_plan();
+    if (!h)
+        return FOF_ERR_OOM;
+    h->nbox = nbox;
+    h->boxes = boxes;
+    if (opt && opt->dense_min > 0) h->dense_min = opt->dense_min;
+    if (opt && opt->retry_cap > 0) h->retry_cap = opt->retry_cap;
+    h->rl = results_layout(nbox);
+    if (workspace) {
+        h->ws = (char*)workspace;
+        h->own_ws = false;
+    } else {
+        cudaError_t e = cudaMalloc((void**)&h->ws, L.total);
+        if (e != cudaSuccess) {
+            delete h;
+            cudaGetLastError();
+            return FOF_ERR_OOM;
+        }
+        h->own_ws = true;
+    }
+    h->ws_bytes = L.total;
+    if (cudaMallocHost((void**)&h->results_host, h->rl.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        fof_destroy(h);
+        return FOF_ERR_OOM;
+    }
+    std::memset(h->results_host, 0, h->rl.bytes);
+    for (int k = 0; k < kNumPhases; ++k) {
+        if (cudaEventCreate(&h->phase[k].ev0) != cudaSuccess ||
+            cudaEventCreate(&h->phase[k].ev1) != cudaSuccess) {
+            fof_destroy(h);
+            return FOF_ERR_CUDA;
+        }
+    }
+    char* ws = h->ws;
+    h->p0.resize(nbox);
+    h->brick0.resize(nbox);
+    for (int i = 0; i < nbox; ++i) {
+        h->p0[i] = boxes[i].p0;
+        h->brick0[i] = boxes[i].brick0;
+    }
+    Geometry& g = h->g;
+    g.boxes = (const BoxDev*)(ws + L.boxes);
+    g.box_p0 = (const int64_t*)(ws + L.p0);
+    g.box_brick0 = (const int64_t*)(ws + L.brick0);
+    g.nbox = nbox;
+    g.total_n = tn;
+    g.total_bricks = tb;
+    g.total_cells = tc;
+    Work& w = h->w;
+    h->results_dev = ws + L.results;
+    w.status = (Status*)(h->results_dev + h->rl.status_off);
+    w.n_groups = (unsigned long long*)(h->results_dev + h->rl.groups_off);
+    w.n_cat = (unsigned long long*)(h->results_dev + h->rl.cat_off);
+    w.bcount = (int*)(ws + L.bcount);
+    w.bstart = (int*)(ws + L.bstart);
+    w.bcursor = (int*)(ws + L.bcursor);
+    w.scan_tmp = (int*)(ws + L.scan_tmp);
+    w.scan_tmp_len = L.scan_len;
+    w.tile_cnt = (int*)(ws + L.tile_cnt);
+    w.tile_off = (int*)(ws + L.tile_off);
+    w.n_tiles = L.n_tiles;
+    w.cell_start = (int*)(ws + L.cell_start);
+    w.tmp = (float4*)(ws + L.tmp);
+    w.sorted = (float4*)(ws + L.sorted);
+    w.parent = (int*)(ws + L.parent);
+    w.minorig = (int*)(ws + L.minorig);
+    w.cnt = (int*)(ws + L.cnt);
+
+    cudaError_t e = cudaMemcpy(ws + L.boxes, boxes.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ws + L.p0, h->p0.data(), 8 * (size_t)nbox, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ws + L.brick0, h->brick0.data(), 8 * (size_t)nbox, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        fof_destroy(h);
+        return cuda_rc(e);
+    }
+    *out = h;
+    return FOF_OK;
+}
+
+int enqueue_link(fof_plan* h, const float* pos, cudaStream_t s)
+{
+    const Geometry& g = h->g;
+    const Work& w = h->w;
+    FOF_TRY(cudaMemsetAsync(h->results_dev, 0, h->rl.bytes, s));
+    if (g.total_n == 0) {
+        h->linked = true;
+        return FOF_OK;
+    }
+    FOF_TRY(cudaMemsetAsync(w.bcount, 0, 4 * (size_t)(g.total_bricks + 1), s));
+    FOF_TRY(cudaMemsetAsync(w.bcursor, 0, 4 * (size_t)(g.total_bricks + 1), s));
+    phase_begin(h, kPhBinCount, s);
+    FOF_TRY(launch_bin_count(pos, g, w, s));
+    phase_end(h, kPhBinCount, s);
+    phase_begin(h, kPhScanBricks, s);
+    FOF_TRY(launch_scan(w.bcount, w.bstart, g.total_bricks, w.scan_tmp, w.scan_tmp_len, s));
+    phase_end(h, kPhScanBricks, s);
+    phase_begin(h, kPhBinScatter, s);
+    FOF_TRY(launch_bin_scatter(pos, g, w, s));
+    phase_end(h, kPhBinScatter, s);
+    phase_begin(h, kPhBrickSort, s);
+    FOF_TRY(launch_brick_sort(g, w, s));
+    phase_end(h, kPhBrickSort, s);
+    phase_begin(h, kPhLink, s);
+    FOF_TRY(launch_link(g, w, h->dense_min, h->retry_cap, s));
+    phase_end(h, kPhLink, s);
+    h->linked = true;
+    return FOF_OK;
+}
+
+int enqueue_groups(fof_plan* h, int32_t* ids, int32_t* sizes, fof_group* cat, int64_t cap,
+                   int32_t min_size, cudaStream_t s)
+{
+    const Geometry& g = h->g;
+    const Work& w = h->w;
+    if (g.total_n > 0) {
+        // status.err is kept from fof_link; counts start from zero
+        FOF_TRY(cudaMemsetAsync(h->results_dev + h->rl.groups_off, 0,
+                                h->rl.bytes - h->rl.groups_off, s));
+        FOF_TRY(cudaMemsetAsync(w.tile_cnt, 0, 4 * (size_t)(w.n_tiles + 1), s));
+        phase_begin(h, kPhFinalize, s);
+        FOF_TRY(launch_finalize(g, w, s));
+        phase_end(h, kPhFinalize, s);
+        phase_begin(h, kPhOutputs, s);
+        FOF_TRY(launch_outputs(g, w, ids, sizes, min_size, s));
+        phase_end(h, kPhOutputs, s);
+        phase_begin(h, kPhCatalogue, s);
+        FOF_TRY(launch_catalogue(g, w, sizes, min_size, (int2*)cat, cap, s));
+        phase_end(h, kPhCatalogue, s);
+    }
+    FOF_TRY(cudaMemcpyAsync(h->results_host, h->results_dev, h->rl.bytes, cudaMemcpyDeviceToHost, s));
+    h->pending = true;
+    h->last_cap = cap;
+    return FOF_OK;
+}
+
+int read_result(fof_plan* h, int64_t* n_groups, int64_t* n_cat, cudaStream_t s)
+{
+    if (!h->pending)
+        return FOF_ERR_STATE;
+    FOF_TRY(cudaStreamSynchronize(s));
+    h->pending = false;
+    collect_times(h);
+    const Status* st = (const Status*)(h->results_host + h->rl.status_off);
+    const long long* ng = (const long long*)(h->results_host + h->rl.groups_off);
+    const long long* nk = (const long long*)(h->results_host + h->rl.cat_off);
+    for (int i = 0; i < h->nbox; ++i) {
+        if (n_groups) n_groups[i] = ng[i];
+        if (n_cat) n_cat[i] = nk[i];
+    }
+    if (st->err & kErrInternal)
+        return FOF_ERR_INTERNAL;
+    if (st->err & kErrRange)
+        return FOF_ERR_RANGE;
+    if (st->err & kErrTimeout)
+        return FOF_ERR_TIMEOUT;
+    if (st->n_cat_total > h->last_cap)
+        return FOF_ERR_CAPACITY;
+    return FOF_OK;
+}
+
+int check_out_args(fof_plan* h, int32_t* ids, int32_t* sizes, fof_group* cat, int64_t cap)
+{
+    if (!h || cap < 0)
+        return FOF_ERR_ARG;
+    if (h->g.total_n > 0 && (!ids || !sizes))
+        return FOF_ERR_ARG;
+    if (cap > 0 && !cat)
+        return FOF_ERR_ARG;
+    return FOF_OK;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+
+extern "C" {
+
+int fof_create(double box, double l_x, int64_t n, fof_handle* out)
+{
+    return create_plan(1, &box, &l_x, &n, nullptr, nullptr, 0, out);
+}
+
+int fof_create_ex(double box, double l_x, int64_t n, const fof_options* opt, void* workspace_dev,
+                  size_t workspace_bytes, fof_handle* out)
+{
+    return create_plan(1, &box, &l_x, &n, opt, workspace_dev, workspace_bytes, out);
+}
+
+size_t fof_workspace_bytes(double box, double l_x, int64_t n, const fof_options* opt)
+{
+    return fof_batch_workspace_bytes(1, &box, &l_x, &n, opt);
+}
+
+int fof_batch_create(int32_t nbox, const double* box, const double* l_x, const int64_t* n,
+                     const fof_options* opt, void* workspace_dev, size_t workspace_bytes,
+                     fof_handle* out)
+{
+    return create_plan(nbox, box, l_x, n, opt, workspace_dev, workspace_bytes, out);
+}
+
+size_t fof_batch_workspace_bytes(int32_t nbox, const double* box, const double* l_x, const int64_t* n,
+                                 const fof_options* opt)
+{
+    std::vector<BoxDev> boxes;
+    int64_t tn, tb, tc;
+    if (setup_batch(nbox, box, l_x, n, opt, boxes, tn, tb, tc) != FOF_OK)
+        return 0;
+    return layout(nbox, tn, tb, tc).total;
+}
+
+int fof_link(fof_handle h, const float* pos_dev, void* stream)
+{
+    if (!h || (h->g.total_n > 0 && !pos_dev))
+        return FOF_ERR_ARG;
+    return enqueue_link(h, pos_dev, (cudaStream_t)stream);
+}
+
+int fof_groups_async(fof_handle h, int32_t* ids_dev, int32_t* sizes_dev, fof_group* catalogue_dev,
+                     int64_t cat_capacity, int32_t min_size, void* stream)
+{
+    int rc = check_out_args(h, ids_dev, sizes_dev, catalogue_dev, cat_capacity);
+    if (rc != FOF_OK)
+        return rc;
+    if (!h->linked)
+        return FOF_ERR_STATE;
+    return enqueue_groups(h, ids_dev, sizes_dev, catalogue_dev, cat_capacity, min_size,
+                          (cudaStream_t)stream);
+}
+
+int fof_result(fof_handle h, int64_t* n_groups_out, int64_t* n_cat_out, void* stream)
+{
+    if (!h)
+        return FOF_ERR_ARG;
+    return read_result(h, n_groups_out, n_cat_out, (cudaStream_t)stream);
+}
+
+int fof_groups(fof_handle h, int32_t* ids_dev, int32_t* sizes_dev, fof_group* catalogue_dev,
+               int64_t cat_capacity, int32_t min_size, int64_t* n_groups_out, int64_t* n_cat_out,
+               void* stream)
+{
+    int rc = fof_groups_async(h, ids_dev, sizes_dev, catalogue_dev, cat_capacity, min_size, stream);
+    if (rc != FOF_OK)
+        return rc;
+    return read_result(h, n_groups_out, n_cat_out, (cudaStream_t)stream);
+}
+
+int fof_run_host(fof_handle h, const float* pos_host, int32_t* ids_host, int32_t* sizes_host,
+                 fof_group* catalogue_host, int64_t cat_capacity, int32_t min_size,
+                 int64_t* n_groups_out, int64_t* n_cat_out, void* stream)
+{
+    if (!h || cat_capacity < 0 || (h->g.total_n > 0 && (!pos_host || !ids_host || !sizes_host)) ||
+        (cat_capacity > 0 && !catalogue_host))
+        return FOF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = h->g.total_n;
+    if (n > 0 && !h->pos_d) {
+        if (cudaMalloc((void**)&h->pos_d, 12 * (size_t)n) != cudaSuccess ||
+            cudaMalloc((void**)&h->ids_d, 4 * (size_t)n) != cudaSuccess ||
+            cudaMalloc((void**)&h->sizes_d, 4 * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            return FOF_ERR_OOM;
+        }
+    }
+    if (cat_capacity > h->cat_d_cap) {
+        if (h->cat_d) cudaFree(h->cat_d);
+        h->cat_d = nullptr;
+        h->cat_d_cap = 0;
+        if (cudaMalloc((void**)&h->cat_d, 8 * (size_t)cat_capacity) != cudaSuccess) {
+            cudaGetLastError();
+            return FOF_ERR_OOM;
+        }
+        h->cat_d_cap = cat_capacity;
+    }
+    if (n > 0)
+        FOF_TRY(cudaMemcpyAsync(h->pos_d, pos_host, 12 * (size_t)n, cudaMemcpyHostToDevice, s));
+    int rc = enqueue_link(h, h->pos_d, s);
+    if (rc != FOF_OK)
+        return rc;
+    rc = enqueue_groups(h, h->ids_d, h->sizes_d, (fof_group*)h->cat_d, cat_capacity, min_size, s);
+    if (rc != FOF_OK)
+        return rc;
+    if (n > 0) {
+        FOF_TRY(cudaMemcpyAsync(ids_host, h->ids_d, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+        FOF_TRY(cudaMemcpyAsync(sizes_host, h->sizes_d, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    }
+    std::vector<int64_t> ng(h->nbox), nk(h->nbox);
+    rc = read_result(h, ng.data(), nk.data(), s);
+    if (rc != FOF_OK && rc != FOF_ERR_CAPACITY)
+        return rc;
+    const Status* st = (const Status*)(h->results_host + h->rl.status_off);
+    int64_t total = st->n_cat_total;
+    int64_t ncopy = total < cat_capacity ? total : cat_capacity;
+    if (ncopy > 0) {
+        FOF_TRY(cudaMemcpyAsync(catalogue_host, h->cat_d, 8 * (size_t)ncopy, cudaMemcpyDeviceToHost, s));
+        FOF_TRY(cudaStreamSynchronize(s));
+    }
+    for (int i = 0; i < h->nbox; ++i) {
+        if (n_groups_out) n_groups_out[i] = ng[i];
+        if (n_cat_out) n_cat_out[i] = nk[i];
+    }
+    return rc;
+}
+
+int fof_graph_build(fof_handle h, const float* pos_dev, int32_t* ids_dev, int32_t* sizes_dev,
+                    fof_group* catalogue_dev, int64_t cat_capacity, int32_t min_size, void* stream)
+{
+    int rc = check_out_args(h, ids_dev, sizes_dev, catalogue_dev, cat_capacity);
+    if (rc != FOF_OK)
+        return rc;
+    if (!stream || (h->g.total_n > 0 && !pos_dev))
+        return FOF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    FOF_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    rc = enqueue_link(h, pos_dev, s);
+    if (rc == FOF_OK)
+        rc = enqueue_groups(h, ids_dev, sizes_dev, catalogue_dev, cat_capacity, min_size, s);
+    h->capturing = false;
+    h->pending = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc != FOF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess)
+        return cuda_rc(e);
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->gexec = nullptr;
+        return cuda_rc(e);
+    }
+    h->graph_cap = cat_capacity;
+    return FOF_OK;
+}
+
+int fof_graph_launch(fof_handle h, void* stream)
+{
+    if (!h || !h->gexec)
+        return h ? FOF_ERR_STATE : FOF_ERR_ARG;
+    FOF_TRY(cudaGraphLaunch(h->gexec, (cudaStream_t)stream));
+    h->linked = true;
+    h->pending = true;
+    h->last_cap = h->graph_cap;
+    // a graph replays every phase once
+    for (int k = 0; k < kNumPhases; ++k) {
+        if (h->g.total_n > 0) {
+            h->launches += kPhaseLaunches[k];
+            h->phase[k].launches += kPhaseLaunches[k];
+        }
+    }
+    return FOF_OK;
+}
+
+int fof_plan_info(fof_handle h, int32_t b, int32_t* cells_per_axis, int32_t* brick_cells,
+                  int32_t* bricks_per_axis)
+{
+    if (!h || b < 0 || b >= h->nbox)
+        return FOF_ERR_ARG;
+    const BoxDev& x = h->boxes[b];
+    if (cells_per_axis) *cells_per_axis = x.nc;
+    if (brick_cells) *brick_cells = x.r;
+    if (bricks_per_axis) *bricks_per_axis = x.nb;
+    return FOF_OK;
+}
+
+int fof_set_timing(fof_handle h, int enable)
+{
+    if (!h)
+        return FOF_ERR_ARG;
+    h->timing = enable != 0;
+    return FOF_OK;
+}
+
+int fof_phase_times(fof_handle h, double* ms, int64_t* launches, const char** names, int max)
+{
+    if (!h)
+        return -FOF_ERR_ARG;
+    collect_times(h);
+    int m = max < kNumPhases ? max : kNumPhases;
+    for (int k = 0; k < m; ++k) {
+        if (ms) ms[k] = h->phase[k].ms;
+        if (launches) launches[k] = h->phase[k].launches;
+        if (names) names[k] = kPhaseNames[k];
+    }
+    return kNumPhases;
+}
+
+int fof_reset_times(fof_handle h)
+{
+    if (!h)
+        return FOF_ERR_ARG;
+    for (int k = 0; k < kNumPhases; ++k) {
+        h->phase[k].ms = 0.0;
+        h->phase[k].launches = 0;
+        h->phase[k].pending = false;
+    }
+    return FOF_OK;
+}
+
+int64_t fof_kernel_launches(fof_handle h)
+{
+    return h ? h->launches : -1;
+}
+
+void fof_destroy(fof_handle h)
+{
+    if (!h)
+        return;
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (int k = 0; k < kNumPhases; ++k) {
+        if (h->phase[k].ev0) cudaEventDestroy(h->phase[k].ev0);
+        if (h->phase[k].ev1) cudaEventDestroy(h->phase[k].ev1);
+    }
+    if (h->pos_d) cudaFree(h->pos_d);
+    if (h->ids_d) cudaFree(h->ids_d);
+    if (h->sizes_d) cudaFree(h->sizes_d);
+    if (h->cat_d) cudaFree(h->cat_d);
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->results_host) cudaFreeHost(h->results_host);
+    delete h;
+}
+
+const char* fof_strerror(int code)
+{
+    switch (code) {
+    case FOF_OK: return "ok";
+    case FOF_ERR_ARG: return "invalid argument";
+    case FOF_ERR_RANGE: return "position outside [0, box) or not finite";
+    case FOF_ERR_CAPACITY: return "catalogue larger than its capacity";
+    case FOF_ERR_STATE: return "call out of order (fof_groups before fof_link)";
+    case FOF_ERR_OOM: return "out of memory";
+    case FOF_ERR_CUDA: return "CUDA runtime error";
+    case FOF_ERR_TIMEOUT: return "union retry limit reached";
+    case FOF_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

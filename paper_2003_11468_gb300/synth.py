@@ -177,31 +177,31 @@ def linking_length(n: int, box: float, b: float = 0.2) -> float:
 
 
 # --------------------------------------------------------------------------
-# Named workloads.  Each returns dict(n, box, l_x, min_size, pos) on demand.
+# Named workloads: dict(name, n, box, l_x, min_size, seed, make(seed=...)).
 # --------------------------------------------------------------------------
 
 def uniform_32k():
     """32^3 particles uniform in the unit box, l_x = 0.2/32, min size 2."""
     n, box = 32 ** 3, 1.0
     return dict(name="fof-32^3-uniform", n=n, box=box,
-                l_x=0.2 * box / 32, min_size=2,
-                make=lambda: uniform_box(n, box, seed=1))
+                l_x=0.2 * box / 32, min_size=2, seed=1,
+                make=lambda seed=1: uniform_box(n, box, seed=seed))
 
 
 def clustered_256():
     """256^3 particles, box 100, 20,000 blobs, l_x = 0.2*100/256, min size 20."""
     n, box = 256 ** 3, 100.0
     return dict(name="fof-256^3-clustered", n=n, box=box,
-                l_x=0.2 * box / 256, min_size=20,
-                make=lambda: clustered_box(n, box, 20000, seed=2))
+                l_x=0.2 * box / 256, min_size=20, seed=2,
+                make=lambda seed=2: clustered_box(n, box, 20000, seed=seed))
 
 
 def clustered_1024():
     """1024^3 particles, box 100, 500,000 blobs, l_x = 0.2*100/1024, min size 20."""
     n, box = 1024 ** 3, 100.0
     return dict(name="fof-1024^3-clustered", n=n, box=box,
-                l_x=0.2 * box / 1024, min_size=20,
-                make=lambda: clustered_box(n, box, 500000, seed=3))
+                l_x=0.2 * box / 1024, min_size=20, seed=3,
+                make=lambda seed=3: clustered_box(n, box, 500000, seed=seed))
 
 
 def clustered_sample_of_1024(k: int = 4):
@@ -214,8 +214,8 @@ def clustered_sample_of_1024(k: int = 4):
     n, box = side ** 3, 100.0 / k
     blobs = max(1, int(round(500000 / k ** 3)))
     return dict(name=f"fof-{side}^3-clustered-sample", n=n, box=box,
-                l_x=0.2 * 100.0 / 1024, min_size=20,
-                make=lambda: clustered_box(n, box, blobs, seed=3000 + k))
+                l_x=0.2 * 100.0 / 1024, min_size=20, seed=3000 + k,
+                make=lambda seed=3000 + k: clustered_box(n, box, blobs, seed=seed))
 
 
 def batch_512(count: int = 512, seed0: int = 4000):
