@@ -137,8 +137,9 @@ int fof_link(fof_handle h, const float *pos_dev, void *stream);
 
 /* Enqueue finalisation and outputs of the last fof_link, then wait for the
  * stream and report.  ids_dev and sizes_dev hold sum(n) int32 each;
- * catalogue_dev holds cat_capacity fof_group entries (may be NULL if
- * cat_capacity is 0).  For a batch, the catalogue is concatenated in box
+ * catalogue_dev holds cat_capacity fof_group entries; NULL (with
+ * cat_capacity 0) asks for no catalogue, whose counts are still reported
+ * and never raise FOF_ERR_CAPACITY.  For a batch, the catalogue is concatenated in box
  * order, min_size applies to every box, and n_groups_out / n_cat_out
  * (host, may be NULL) receive one count per box.  If the catalogue has more
  * than cat_capacity entries in total, the first cat_capacity are written,

@@ -463,7 +463,7 @@ int enqueue_groups(fof_plan* h, int32_t* ids, int32_t* sizes, fof_group* cat, in
     }
     FOF_TRY(cudaMemcpyAsync(h->results_host, h->results_dev, h->rl.bytes, cudaMemcpyDeviceToHost, s));
     h->pending = true;
-    h->last_cap = cap;
+    h->last_cap = cat ? cap : INT64_MAX;     // no catalogue wanted: no capacity error
     return FOF_OK;
 }
 
@@ -671,7 +671,7 @@ int fof_graph_build(fof_handle h, const float* pos_dev, int32_t* ids_dev, int32_
         h->gexec = nullptr;
         return cuda_rc(e);
     }
-    h->graph_cap = cat_capacity;
+    h->graph_cap = catalogue_dev ? cat_capacity : INT64_MAX;
     return FOF_OK;
 }
 
