@@ -67,7 +67,8 @@ enum {
     FOF_ERR_OOM = 5,       /* device or pinned-host allocation failed        */
     FOF_ERR_CUDA = 6,      /* a CUDA runtime call failed                     */
     FOF_ERR_TIMEOUT = 7,   /* a bounded retry loop ran out (union CAS)       */
-    FOF_ERR_INTERNAL = 8   /* a device-side consistency check failed         */
+    FOF_ERR_INTERNAL = 8,  /* a device-side consistency check failed         */
+    FOF_ERR_TOO_LARGE = 9  /* problem exceeds fof_run_noalloc's fixed scratch */
 };
 
 typedef struct fof_plan *fof_handle;    /* opaque, owned by the library */
@@ -207,6 +208,37 @@ int64_t fof_kernel_launches(fof_handle h);
 
 void fof_destroy(fof_handle h);
 const char *fof_strerror(int code);
+
+/* ---------------------------------------------------------------------- */
+/* allocation-free single-box run                                          */
+/* ---------------------------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: a host application that owns, and has
+ * already handed out, all GPU memory (N-body codes typically leave little
+ * free for an on-the-fly group finder), or a time-step loop that must not
+ * call cudaMalloc/cudaFree because they synchronise the whole device.
+ *
+ * Runs fof_link + fof_groups for ONE box with the same arguments, outputs
+ * and errors as fof_create + fof_link + fof_groups, but allocates nothing:
+ * no cudaMalloc/cudaFree, no pinned memory, no events, no plan.  The
+ * workspace is a fixed 32 MiB array in the library's own device memory,
+ * which every GPU that loads the library holds until the process exits.
+ *   - Problems whose workspace (fof_workspace_bytes with NULL options)
+ *     exceeds 32 MiB are rejected with FOF_ERR_TOO_LARGE, checked before any
+ *     pointer; that is about 600,000 particles at the default occupancy.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and overwrites it (the
+ *     call clears what must start at zero).  Calls whose GPU work overlaps,
+ *     from several host threads or on several streams, race and give wrong
+ *     results: serialise them.
+ *   - Blocking: returns after the stream has finished the work. */
+int fof_run_noalloc(double box, double l_x, int64_t n, const float *pos_dev,
+                    int32_t *ids_dev, int32_t *sizes_dev, fof_group *catalogue_dev,
+                    int64_t cat_capacity, int32_t min_size, int64_t *n_groups_out,
+                    int64_t *n_cat_out, void *stream);
 
 #ifdef __cplusplus
 }

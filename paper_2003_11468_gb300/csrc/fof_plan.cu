@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -774,8 +775,142 @@ const char* fof_strerror(int code)
     case FOF_ERR_CUDA: return "CUDA runtime error";
     case FOF_ERR_TIMEOUT: return "union retry limit reached";
     case FOF_ERR_INTERNAL: return "internal consistency check failed";
+    case FOF_ERR_TOO_LARGE: return "problem needs more than the fixed scratch of fof_run_noalloc";
     default: return "unknown error";
     }
 }
 
 }  // extern "C"
+
+// ==========================================================================
+// fof_run_noalloc: one box, whole pipeline, no allocation of any kind.
+//
+// For callers that cannot allocate device memory: a host application that
+// owns (and has already handed out) all GPU memory, or a loop that must not
+// call cudaMalloc/cudaFree because they synchronise the device.  The
+// workspace is the file-scope array below instead of a plan's allocation.
+// ==========================================================================
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)32 << 20;   // 32 MiB per device
+constexpr int kNoallocMaxDevices = 64;
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_noalloc_mu;
+char* g_noalloc_ptr[kNoallocMaxDevices];   // device address of the array, per device
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a stand-in, so the address is looked up once per
+// device with that device current.
+int noalloc_scratch(char** out)
+{
+    int dev = 0;
+    FOF_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return FOF_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        FOF_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = (char*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return FOF_OK;
+}
+
+}  // namespace
+
+extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* pos_dev,
+                               int32_t* ids_dev, int32_t* sizes_dev, fof_group* catalogue_dev,
+                               int64_t cat_capacity, int32_t min_size, int64_t* n_groups_out,
+                               int64_t* n_cat_out, void* stream)
+{
+    if (cat_capacity < 0 || (cat_capacity > 0 && !catalogue_dev))
+        return FOF_ERR_ARG;
+    BoxDev b;
+    int rc = setup_box(box, l_x, n, nullptr, b);
+    if (rc != FOF_OK)
+        return rc;
+    const int64_t tb = (int64_t)b.nb * b.nb * b.nb;
+    const int64_t tc = tb * (int64_t)b.r * b.r * b.r;
+    const Layout L = layout(1, n, tb, tc);
+    if (L.total > kNoallocScratchBytes)
+        return FOF_ERR_TOO_LARGE;
+    if (n > 0 && (!pos_dev || !ids_dev || !sizes_dev))
+        return FOF_ERR_ARG;
+    char* ws = nullptr;
+    rc = noalloc_scratch(&ws);
+    if (rc != FOF_OK)
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const ResultsLayout rl = results_layout(1);
+
+    Geometry g{};
+    g.boxes = (const BoxDev*)(ws + L.boxes);
+    g.box_p0 = (const int64_t*)(ws + L.p0);
+    g.box_brick0 = (const int64_t*)(ws + L.brick0);
+    g.nbox = 1;
+    g.total_n = n;
+    g.total_bricks = tb;
+    g.total_cells = tc;
+    Work w{};
+    char* res = ws + L.results;
+    w.status = (Status*)(res + rl.status_off);
+    w.n_groups = (unsigned long long*)(res + rl.groups_off);
+    w.n_cat = (unsigned long long*)(res + rl.cat_off);
+    w.bcount = (int*)(ws + L.bcount);
+    w.bstart = (int*)(ws + L.bstart);
+    w.bcursor = (int*)(ws + L.bcursor);
+    w.scan_tmp = (int*)(ws + L.scan_tmp);
+    w.scan_tmp_len = L.scan_len;
+    w.tile_cnt = (int*)(ws + L.tile_cnt);
+    w.tile_off = (int*)(ws + L.tile_off);
+    w.n_tiles = L.n_tiles;
+    w.cell_start = (int*)(ws + L.cell_start);
+    w.tmp = (float4*)(ws + L.tmp);
+    w.sorted = (float4*)(ws + L.sorted);
+    w.parent = (int*)(ws + L.parent);
+    w.minorig = (int*)(ws + L.minorig);
+    w.cnt = (int*)(ws + L.cnt);
+
+    // The array keeps the previous call's contents: the box table is
+    // rewritten and every counter that must start at zero is cleared here.
+    const int64_t zero = 0;
+    FOF_TRY(cudaMemcpyAsync(ws + L.boxes, &b, sizeof(BoxDev), cudaMemcpyHostToDevice, s));
+    FOF_TRY(cudaMemcpyAsync(ws + L.p0, &zero, sizeof(zero), cudaMemcpyHostToDevice, s));
+    FOF_TRY(cudaMemcpyAsync(ws + L.brick0, &zero, sizeof(zero), cudaMemcpyHostToDevice, s));
+    FOF_TRY(cudaMemsetAsync(res, 0, rl.bytes, s));
+    if (n > 0) {
+        FOF_TRY(cudaMemsetAsync(w.bcount, 0, 4 * (size_t)(tb + 1), s));
+        FOF_TRY(cudaMemsetAsync(w.bcursor, 0, 4 * (size_t)(tb + 1), s));
+        FOF_TRY(cudaMemsetAsync(w.tile_cnt, 0, 4 * (size_t)(w.n_tiles + 1), s));
+        FOF_TRY(launch_bin_count(pos_dev, g, w, s));
+        FOF_TRY(launch_scan(w.bcount, w.bstart, tb, w.scan_tmp, w.scan_tmp_len, s));
+        FOF_TRY(launch_bin_scatter(pos_dev, g, w, s));
+        FOF_TRY(launch_brick_sort(g, w, s));
+        FOF_TRY(launch_link(g, w, kDefaultDenseMin, kDefaultRetryCap, s));
+        FOF_TRY(launch_finalize(g, w, s));
+        FOF_TRY(launch_outputs(g, w, ids_dev, sizes_dev, min_size, s));
+        FOF_TRY(launch_catalogue(g, w, sizes_dev, min_size, (int2*)catalogue_dev, cat_capacity, s));
+    }
+    alignas(16) unsigned char host_res[128];
+    FOF_TRY(cudaMemcpyAsync(host_res, res, rl.bytes, cudaMemcpyDeviceToHost, s));
+    FOF_TRY(cudaStreamSynchronize(s));
+    const Status* st = (const Status*)(host_res + rl.status_off);
+    const long long* ng = (const long long*)(host_res + rl.groups_off);
+    const long long* nk = (const long long*)(host_res + rl.cat_off);
+    if (n_groups_out) *n_groups_out = ng[0];
+    if (n_cat_out) *n_cat_out = nk[0];
+    if (st->err & kErrInternal)
+        return FOF_ERR_INTERNAL;
+    if (st->err & kErrRange)
+        return FOF_ERR_RANGE;
+    if (st->err & kErrTimeout)
+        return FOF_ERR_TIMEOUT;
+    if (catalogue_dev && st->n_cat_total > cat_capacity)
+        return FOF_ERR_CAPACITY;
+    return FOF_OK;
+}

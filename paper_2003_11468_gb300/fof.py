@@ -26,6 +26,7 @@ FOF_ERR_OOM = 5
 FOF_ERR_CUDA = 6
 FOF_ERR_TIMEOUT = 7
 FOF_ERR_INTERNAL = 8
+FOF_ERR_TOO_LARGE = 9
 
 
 class fof_options(ctypes.Structure):
@@ -82,6 +83,7 @@ def load():
             "fof_kernel_launches": ([P], i64),
             "fof_destroy": ([P], None),
             "fof_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "fof_run_noalloc": ([f64, f64, i64, P, P, P, P, i64, i32, P, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -254,6 +256,20 @@ def fof_kernel_launches(h) -> int:
 def fof_destroy(h) -> None:
     if h:
         load().fof_destroy(h)
+
+
+def fof_run_noalloc(box, l_x, n, pos, ids, sizes, catalogue, cat_capacity, min_size, stream=None,
+                    allow_capacity=False):
+    """Allocation-free single-box run (see include/fof.h).  Returns
+    (code, n_groups, n_cat)."""
+    ng = ctypes.c_int64(0)
+    nk = ctypes.c_int64(0)
+    code = load().fof_run_noalloc(box, l_x, n, _ptr(pos), _ptr(ids), _ptr(sizes), _ptr(catalogue),
+                                  cat_capacity, min_size, ctypes.byref(ng), ctypes.byref(nk),
+                                  _stream(stream))
+    if code != FOF_OK and not (allow_capacity and code == FOF_ERR_CAPACITY):
+        raise FoFError(code, "fof_run_noalloc")
+    return code, ng.value, nk.value
 
 
 # ---------------------------------------------------------------------------

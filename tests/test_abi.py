@@ -49,7 +49,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_strerror_and_argument_errors(lib):
     from paper_2003_11468_gb300 import fof
     assert fof.strerror(0) == "ok"
-    for code in range(1, 9):
+    for code in range(1, 10):
         assert fof.strerror(code) != "unknown error"
     h = ctypes.c_void_p()
     # invalid geometry is rejected before any device call
