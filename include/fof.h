@@ -82,11 +82,13 @@ typedef struct {
 typedef struct {
     int32_t cells_per_axis;  /* cells per box side; must keep side >= l_x   */
     int32_t brick_cells;     /* cells per brick side: 1, 2, 4, 8 or 16      */
-    double occupancy;        /* target mean particles per cell (default 1.0) */
-    int32_t dense_min;       /* cell occupancy from which a warp links the
-                                cell cooperatively with root skipping        */
+    double occupancy;        /* target mean particles per cell (default 0.5) */
+    int32_t dense_min;       /* cell occupancy from which a cell is split
+                                into sub-cells and linked in shared memory
+                                (default 256)                                */
     int32_t retry_cap;       /* max CAS attempts per union (default 2^20)    */
-    int32_t reserved[4];
+    int32_t reserved[4];     /* [0]: occupancy from which a warp links a cell
+                                as a team (default 8); others must be 0      */
 } fof_options;
 
 /* ---------------------------------------------------------------------- */
@@ -188,6 +190,21 @@ int fof_graph_launch(fof_handle h, void *stream);
 /* ---------------------------------------------------------------------- */
 /* introspection                                                           */
 /* ---------------------------------------------------------------------- */
+
+/* Geometry the library derives for one box (host only, no device call).
+ * Cells per axis nc, cells per brick side, bricks per axis; sub-cells per
+ * cell side q (1 = cells are never split) and fine cells per axis nc*q;
+ * inv_fine = float32(nc*q / box), so a coordinate's fine index is
+ * min(nc*q - 1, (int)(x * inv_fine)) with a float32 multiply and its cell
+ * index is the fine one divided by q; xmax = largest valid coordinate;
+ * t_lo / t_hi = float32 squared-distance bounds of the pre-test.
+ * Returns FOF_OK or FOF_ERR_ARG (same rules as fof_create_ex). */
+typedef struct {
+    int32_t cells_per_axis, brick_cells, bricks_per_axis, sub_cells, fine_per_axis;
+    float inv_fine, xmax, t_lo, t_hi;
+} fof_geometry;
+
+int fof_box_geometry(double box, double l_x, int64_t n, const fof_options *opt, fof_geometry *out);
 
 /* Plan geometry of box b: cells per axis, cells per brick side, number of
  * bricks per axis.  Any pointer may be NULL. */

@@ -48,6 +48,8 @@ def _load():
             i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int32
             lib.fof_oracle_linked.argtypes = [P, P, f64, f64]
             lib.fof_oracle_linked.restype = ctypes.c_int
+            lib.fof_oracle_linked_many.argtypes = [i64, P, P, f64, f64, P]
+            lib.fof_oracle_linked_many.restype = None
             lib.fof_oracle_groups.argtypes = [i64, P, f64, f64, P, P]
             lib.fof_oracle_groups.restype = ctypes.c_int
             lib.fof_oracle_brute.argtypes = [i64, P, f64, f64, P]
@@ -76,6 +78,14 @@ def linked(a, b, box: float, l_x: float) -> bool:
     pa = np.ascontiguousarray(a, dtype=np.float32).reshape(3)
     pb = np.ascontiguousarray(b, dtype=np.float32).reshape(3)
     return bool(_load().fof_oracle_linked(_ptr(pa), _ptr(pb), float(box), float(l_x)))
+
+
+def linked_many(a, b, box: float, l_x: float) -> np.ndarray:
+    """The predicate for each pair of rows of a and b (float32 [m, 3])."""
+    pa, pb = _pos(a), _pos(b)
+    out = np.empty(pa.shape[0], dtype=np.uint8)
+    _load().fof_oracle_linked_many(pa.shape[0], _ptr(pa), _ptr(pb), float(box), float(l_x), _ptr(out))
+    return out.astype(bool)
 
 
 def groups(pos, box: float, l_x: float):

@@ -26,6 +26,7 @@
  *
  * Entry points:
  *   fof_oracle_linked      the predicate itself (for pinning tests)
+ *   fof_oracle_linked_many the predicate over arrays of pairs
  *   fof_oracle_groups      cell list + breadth-first search, all particles
  *   fof_oracle_brute       O(N^2) pair loop + serial union-find (tiny N)
  *   fof_oracle_component   breadth-first search of one particle's group
@@ -67,6 +68,15 @@ int fof_oracle_linked(const float *a, const float *b, double box, double l_x)
 {
     double l2 = l_x * l_x;
     return linked(a, b, box, l2);
+}
+
+/* out[k] = the predicate for the pair (a[k], b[k]), k < m */
+void fof_oracle_linked_many(int64_t m, const float *a, const float *b, double box, double l_x,
+                            uint8_t *out)
+{
+    double l2 = l_x * l_x;
+    for (int64_t k = 0; k < m; ++k)
+        out[k] = (uint8_t)linked(a + 3 * k, b + 3 * k, box, l2);
 }
 
 /* ------------------------------------------------------------------ */

@@ -202,7 +202,10 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
                                                              int* __restrict__ minorig,
                                                              int* __restrict__ cnt,
                                                              int* __restrict__ cell_start,
-                                                             int* __restrict__ err)
+                                                             int* __restrict__ err,
+                                                             int64_t* __restrict__ dense_list,
+                                                             int* __restrict__ n_dense,
+                                                             int dense_min)
 {
     __shared__ int hist[kMaxR3];
     __shared__ int sw[32];
@@ -233,6 +236,8 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
             hist[c] = ex;                       // becomes the cursor
             cell_start[cbase + c] = s0 + ex;
             ex += h;
+            if (is_sub(h, b, dense_min))
+                dense_list[atomicAdd(n_dense, 1)] = cbase + c;
         }
         __syncthreads();
         for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
@@ -303,7 +308,7 @@ cudaError_t launch_bin_scatter(const float* pos, const Geometry& g, const Work& 
     return cudaGetLastError();
 }
 
-cudaError_t launch_brick_sort(const Geometry& g, const Work& w, cudaStream_t s)
+cudaError_t launch_brick_sort(const Geometry& g, const Work& w, int dense_min, cudaStream_t s)
 {
     if (g.total_bricks == 0)
         return cudaSuccess;
@@ -312,7 +317,8 @@ cudaError_t launch_brick_sort(const Geometry& g, const Work& w, cudaStream_t s)
     if (blocks > cap) blocks = cap;
     k_brick_sort<<<(unsigned)blocks, kSortThreads, 0, s>>>(g, w.tmp, w.bstart, w.sorted, w.parent,
                                                          w.minorig, w.cnt, w.cell_start,
-                                                         &w.status->err);
+                                                         &w.status->err, w.dense_list, w.n_dense,
+                                                         dense_min);
     return cudaGetLastError();
 }
 

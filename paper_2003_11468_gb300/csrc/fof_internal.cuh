@@ -37,13 +37,24 @@ struct BoxDev {
     int32_t r;        // cells per brick per axis (power of two)
     int32_t log2r;
     int32_t nc;       // cells per axis = nb * r
-    float inv_h;      // float32(nc / L): cell index = min(nc-1, (int)(x * inv_h))
+    int32_t q;        // sub-cells per cell axis (1: cells are not split)
+    int32_t nf;       // fine cells per axis = nc * q
+    uint32_t magic_q; // ceil(2^32 / q): g / q == __umulhi(g, magic_q) for g < 2^14
+    float inv_hf;     // float32(nf / L): fine index = min(nf-1, (int)(x * inv_hf))
     float Lf;         // float32(L) for the float32 pre-test
     float xmax;       // largest float32 strictly below L (valid: 0 <= x <= xmax)
     float t_lo;       // pre-test: d2f < t_lo  => linked
     float t_hi;       // pre-test: d2f > t_hi  => not linked
-    int32_t pad;
+    float reach2;     // (l_x / hf)^2 (1 + 2^-6): a sub-cell whose box is farther
+                      // than this (in fine units, squared) holds no partner
+    int32_t team_min; // occupancy from which k_link links a cell as a warp team
 };
+
+// A cell is "subdivided" (linked by the dense kernels) when its box splits
+// cells (q > 1) and it holds between dense_min and kDenseMax particles.
+constexpr int kDenseMax = 3072;   // particles of a subdivided cell (shared memory)
+constexpr int kMaxQ = 12;
+constexpr int kMaxQ3 = kMaxQ * kMaxQ * kMaxQ;
 
 // Per-run device status.
 struct Status {
@@ -70,16 +81,27 @@ __device__ __forceinline__ int box_of(const int64_t* __restrict__ starts, int nb
 // cells
 // ------------------------------------------------------------------------
 
-// Cell coordinate along one axis.  With cell side h = L/nc >= l_x (1 + 2^-9)
-// and nc <= 4096, the float32 rounding of x * inv_h moves a coordinate by at
-// most nc * 2^-23 < 2^-10 cells, so two coordinates that the exact predicate
-// links land in the same or in periodically adjacent cells.  Clamping keeps
-// every input (even an invalid one) inside the grid.
+// Fine coordinate along one axis: (int)fl32(x * fl32(nf / L)), clamped so
+// that every input (even an invalid one) stays inside the grid.  The cell
+// coordinate is the fine one divided by q; the margins that make linked
+// pairs land in adjacent cells (and sub-cells within +-2, and sub-cells
+// cliques) are derived in fof_plan.cu (setup_box).
+__device__ __forceinline__ int fine_coord(float x, const BoxDev& b)
+{
+    int c = (int)__fmul_rn(x, b.inv_hf);
+    c = c < 0 ? 0 : c;
+    return c > b.nf - 1 ? b.nf - 1 : c;
+}
+
 __device__ __forceinline__ int cell_coord(float x, const BoxDev& b)
 {
-    int c = (int)__fmul_rn(x, b.inv_h);
-    c = c < 0 ? 0 : c;
-    return c > b.nc - 1 ? b.nc - 1 : c;
+    int g = fine_coord(x, b);
+    return b.q == 1 ? g : (int)__umulhi((unsigned)g, b.magic_q);
+}
+
+__device__ __forceinline__ bool is_sub(int m, const BoxDev& b, int dense_min)
+{
+    return b.q > 1 && m >= dense_min && m <= kDenseMax;
 }
 
 __device__ __forceinline__ uint32_t spread3(uint32_t v)   // 5 bits -> every 3rd bit
@@ -271,6 +293,10 @@ struct Work {
     Status* status;     // device status
     unsigned long long* n_groups;  // [nbox]
     unsigned long long* n_cat;     // [nbox]
+    int64_t* dense_list; // [dense_cap] cell keys of the subdivided cells
+    int* n_dense;        // number of entries in dense_list
+    int* dense_root;     // [total_n / dense_min + 1] by first slot / dense_min:
+                         // root of a subdivided cell that is one group, else -1
 };
 
 constexpr int kCatTile = 2048;  // labels per catalogue tile
@@ -282,7 +308,10 @@ cudaError_t launch_scan(const int* in, int* out, int64_t len, int* tmp, int64_t 
                         cudaStream_t s);
 int64_t scan_tmp_elems(int64_t len);
 cudaError_t launch_bin_scatter(const float* pos, const Geometry& g, const Work& w, cudaStream_t s);
-cudaError_t launch_brick_sort(const Geometry& g, const Work& w, cudaStream_t s);
+cudaError_t launch_brick_sort(const Geometry& g, const Work& w, int dense_min, cudaStream_t s);
+cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, int retry_cap, bool pairs,
+                         cudaStream_t s);
+size_t dense_smem();
 cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, int retry_cap,
                         cudaStream_t s);
 cudaError_t launch_finalize(const Geometry& g, const Work& w, cudaStream_t s);

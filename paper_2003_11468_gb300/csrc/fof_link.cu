@@ -7,7 +7,7 @@
 // visited once; inside the own cell only partners with a larger slot are
 // tested.
 //
-// Dense cells (at least `dense_min` particles) are linked by the warp as a
+// Cells with at least team_min particles are linked by the warp as a
 // team: the lanes that belong to the cell keep their current root, the
 // candidates of a neighbour cell are loaded 32 at a time (coalesced float4)
 // with a snapshot of their roots, and
@@ -15,6 +15,13 @@
 //   * a single candidate is skipped when every lane's root equals its root,
 // which is exact because groups only ever merge: two particles whose roots
 // were once equal stay in one group.  Sparse particles search on their own.
+//
+// Cells that the dense kernels link (subdivided cells, fof_dense.cu) are
+// skipped here, as own cells and as neighbours: every pair that involves
+// one of them belongs to a dense task.  Where the box has sub-cells, a
+// linked pair is at most 2 fine cells apart on each axis, so a particle
+// only visits the forward neighbours across faces it lies within 2 fine
+// cells of (exact pruning of the stencil).
 //
 // Linked pairs are merged with the CAS union of fof_internal.cuh.
 #include "fof_internal.cuh"
@@ -48,6 +55,31 @@ __device__ __forceinline__ bool nbr_duplicate(const BoxDev& b, const Cell& c, in
         if (nbr_key(b, c, q) == key)
             return true;
     return false;
+}
+
+// The forward neighbours particle p can reach.  With sub-cells (q > 1) a
+// linked pair is at most 2 fine cells apart on each axis, so p needs the
+// neighbour across a face only when it sits within 2 fine cells of that
+// face; without sub-cells every neighbour is kept.  Bit k = fwd_offset(k).
+__device__ __forceinline__ unsigned reach_mask(const float4& p, const BoxDev& b, const Cell& c)
+{
+    if (b.q == 1)
+        return 0x1fffu;
+    const int q = b.q;
+    const int lx = fine_coord(p.x, b) - c.cx * q;
+    const int ly = fine_coord(p.y, b) - c.cy * q;
+    const int lz = fine_coord(p.z, b) - c.cz * q;
+    const bool hx = lx >= q - 2, hy = ly >= q - 2, hz = lz >= q - 2;
+    const bool wx = lx <= 1, wy = ly <= 1;
+    unsigned m = 0;
+    for (int k = 0; k < 13; ++k) {
+        int dx, dy, dz;
+        fwd_offset(k, dx, dy, dz);
+        bool ok = (dx == 0 || (dx > 0 ? hx : wx)) && (dy == 0 || (dy > 0 ? hy : wy)) &&
+                  (dz == 0 || hz);            // dz is never negative in the half stencil
+        m |= (unsigned)ok << k;
+    }
+    return m;
 }
 
 __device__ __forceinline__ float4 shfl4(float4 v, int src)
@@ -120,7 +152,8 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
             c0 = cell_start[self];
             c1 = cell_start[self + 1];
         }
-        const bool dense = valid && (c1 - c0) >= dense_min;
+        const bool sub = valid && is_sub(c1 - c0, g.boxes[bi], dense_min);
+        const bool dense = valid && !sub && (c1 - c0) >= g.boxes[bi].team_min;
         unsigned dmask = __ballot_sync(kFull, dense);
 
         // ---- dense cells: the whole warp links each cell as a team ----
@@ -143,26 +176,34 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
                 int end = __shfl_sync(kFull, c1, lead);
                 team_link(parent, sorted, b, mine, s, p, ri, first + 1, end, true, cap, err);
             }
+            const unsigned reach = mine ? reach_mask(p, b, tc) : 0u;
+            const unsigned team_reach = __reduce_or_sync(kFull, reach);
             for (int k = 0; k < 13; ++k) {
-                if (nbr_duplicate(b, tc, k, key))
+                if (!((team_reach >> k) & 1u) || nbr_duplicate(b, tc, k, key))
                     continue;
                 int64_t nk = nbr_key(b, tc, k);
                 int j0 = cell_start[nk], j1 = cell_start[nk + 1];
-                team_link(parent, sorted, b, mine, s, p, ri, j0, j1, false, cap, err);
+                if (is_sub(j1 - j0, b, dense_min))
+                    continue;
+                team_link(parent, sorted, b, mine && ((reach >> k) & 1u), s, p, ri, j0, j1, false,
+                          cap, err);
             }
         }
 
         // ---- sparse cells: every lane on its own ----
-        if (valid && !dense) {
+        if (valid && !dense && !sub) {
             const BoxDev& b = g.boxes[bi];
             for (int j = (int)s + 1; j < c1; ++j)
                 if (linked(p, sorted[j], b))
                     uf_union(parent, (int)s, j, cap, err);
+            const unsigned reach = reach_mask(p, b, c);
             for (int k = 0; k < 13; ++k) {
-                if (nbr_duplicate(b, c, k, self))
+                if (!((reach >> k) & 1u) || nbr_duplicate(b, c, k, self))
                     continue;
                 int64_t nk = nbr_key(b, c, k);
                 int j0 = cell_start[nk], j1 = cell_start[nk + 1];
+                if (is_sub(j1 - j0, b, dense_min))
+                    continue;
                 for (int j = j0; j < j1; ++j)
                     if (linked(p, sorted[j], b))
                         uf_union(parent, (int)s, j, cap, err);

@@ -37,20 +37,23 @@ int sm_count()
 namespace {
 
 enum Phase {
-    kPhBinCount, kPhScanBricks, kPhBinScatter, kPhBrickSort, kPhLink,
+    kPhBinCount, kPhScanBricks, kPhBinScatter, kPhBrickSort, kPhDenseSelf, kPhDensePairs, kPhLink,
     kPhFinalize, kPhOutputs, kPhCatalogue, kNumPhases
 };
 
 const char* kPhaseNames[kNumPhases] = {
-    "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "link",
+    "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "dense_self", "dense_pairs", "link",
     "finalize", "outputs", "catalogue",
 };
-const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 1, 1, 1, 4};
+const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 1, 1, 1, 1, 1, 4};
 
 constexpr int64_t kMaxTotal = 2147483646LL;   // slots and labels are int32
 constexpr int kDefaultRetryCap = 1 << 20;
-constexpr int kDefaultDenseMin = 24;
-constexpr int kMaxCellsPerAxis = 4096;        // float32 cell-index precision
+constexpr int kDefaultDenseMin = 256;
+constexpr double kDefaultOccupancy = 0.5;
+constexpr int kDefaultTeamMin = 8;
+constexpr int kMaxCellsPerAxis = 4096;        // float32 cell-index precision (unsplit cells)
+constexpr int kMaxFinePerAxis = 16384;        // float32 index precision (sub-cells)
 
 // Results block (device and pinned host copy): status, then per-box counts.
 struct ResultsLayout {
@@ -121,7 +124,7 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
             return FOF_ERR_ARG;
         nc = o->cells_per_axis;
     } else {
-        double occ = (o && o->occupancy > 0.0) ? o->occupancy : 1.0;
+        double occ = (o && o->occupancy > 0.0) ? o->occupancy : kDefaultOccupancy;
         double t = std::floor(std::cbrt((double)n / occ));
         nc = t < 1.0 ? 1 : (int64_t)t;
         if (nc > nc_max) nc = nc_max;
@@ -139,6 +142,28 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
     int64_t nb = nc / r;
     nc = nb * r;
 
+    // Sub-cells.  q sub-cells per cell side, fine side hf = h/q with
+    //   l_x (1 + 2^-7) / 2 <= hf <= l_x / (sqrt(3) (1 + 2^-7)),
+    // nf = nc q <= 16384 fine cells per axis and nc >= 3.  The fine index
+    // (int)fl32(x * fl32(nf/L)) is within nf 2^-23 <= 2^-9 fine cells of
+    // x nf / L, so (a) the members of one fine cell span at most
+    // hf (1 + 2^-8) per axis, a diameter below sqrt(3) hf (1 + 2^-8) <
+    // l_x (1 - 2^-9): every pair inside a fine cell is linked exactly; and
+    // (b) a linked pair, at most l_x (1 + 2^-50) <= hf (2 - 2^-6) apart per
+    // axis, has fine indices at most 2 apart, hence cell indices at most 1
+    // apart.  When no q meets these bounds the box keeps q = 1 and cells
+    // are never split.
+    int qs = 1;
+    {
+        double h = L / (double)nc;
+        double want = std::ceil(h * std::sqrt(3.0) * (1.0 + std::ldexp(1.0, -7)) / l_x);
+        if (want >= 2.0 && want <= kMaxQ && nc >= 3 && nc * (int64_t)want <= kMaxFinePerAxis) {
+            double hf = h / want;
+            if (hf >= l_x * (1.0 + std::ldexp(1.0, -7)) / 2.0 &&
+                hf * std::sqrt(3.0) * (1.0 + std::ldexp(1.0, -7)) <= l_x)
+                qs = (int)want;
+        }
+    }
     b.n = n;
     b.L = L;
     b.l2 = l_x * l_x;
@@ -146,8 +171,21 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
     b.r = r;
     b.log2r = log2r;
     b.nc = (int32_t)nc;
-    b.inv_h = (float)((double)nc / L);
+    b.q = qs;
+    b.nf = (int32_t)(nc * qs);
+    b.magic_q = qs > 1 ? (uint32_t)((((uint64_t)1 << 32) + qs - 1) / qs) : 0u;
+    b.inv_hf = (float)((double)b.nf / L);
     b.Lf = (float)L;
+    // A partner of p lies within l_x (1 + 2^-50) of p.  The gap between p and
+    // a sub-cell, measured from p's float32 fine coordinate (error below
+    // 2^-8 fine units, both roundings included), underestimates the true gap
+    // by less than 2^-8 per axis; comparing its square with
+    // (l_x/hf + 2^-6)^2 therefore never drops a sub-cell holding a partner.
+    {
+        double rf = l_x / (L / (double)b.nf) + std::ldexp(1.0, -6);
+        b.reach2 = (float)(rf * rf * (1.0 + std::ldexp(1.0, -20)));
+    }
+    b.team_min = (o && o->reserved[0] > 0) ? o->reserved[0] : kDefaultTeamMin;
     b.xmax = (float)L;
     while ((double)b.xmax >= L) b.xmax = std::nextafter(b.xmax, 0.0f);
 
@@ -208,11 +246,12 @@ namespace {
 
 struct Layout {
     size_t boxes, p0, brick0, results, bcount, bstart, bcursor, scan_tmp, tile_cnt, tile_off,
-        cell_start, tmp, sorted, parent, minorig, cnt, total;
-    int64_t scan_len, n_tiles;
+        cell_start, tmp, sorted, parent, minorig, cnt, dense_list, n_dense, dense_root, total;
+    int64_t scan_len, n_tiles, dense_cap;
 };
 
-Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cells)
+Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cells,
+              int dense_min = kDefaultDenseMin)
 {
     Layout L{};
     size_t off = 0;
@@ -240,8 +279,17 @@ Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cel
     L.parent = take(4 * (size_t)total_n);
     L.minorig = take(4 * (size_t)total_n);
     L.cnt = take(4 * (size_t)total_n);
+    L.dense_cap = total_n / dense_min + 1;
+    L.dense_list = take(8 * (size_t)L.dense_cap);
+    L.n_dense = take(4);
+    L.dense_root = take(4 * (size_t)(total_n / dense_min + 2));
     L.total = off;
     return L;
+}
+
+int dense_min_of(const fof_options* opt)
+{
+    return (opt && opt->dense_min > 0) ? opt->dense_min : kDefaultDenseMin;
 }
 
 int setup_batch(int32_t nbox, const double* box, const double* l_x, const int64_t* n,
@@ -326,7 +374,7 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     int rc = setup_batch(nbox, box, l_x, n, opt, boxes, tn, tb, tc);
     if (rc != FOF_OK)
         return rc;
-    Layout L = layout(nbox, tn, tb, tc);
+    Layout L = layout(nbox, tn, tb, tc, dense_min_of(opt));
     if (workspace && (workspace_bytes < L.total || ((uintptr_t)workspace & 255u)))
         return FOF_ERR_ARG;
 
@@ -398,6 +446,9 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     w.parent = (int*)(ws + L.parent);
     w.minorig = (int*)(ws + L.minorig);
     w.cnt = (int*)(ws + L.cnt);
+    w.dense_list = (int64_t*)(ws + L.dense_list);
+    w.n_dense = (int*)(ws + L.n_dense);
+    w.dense_root = (int*)(ws + L.dense_root);
 
     cudaError_t e = cudaMemcpy(ws + L.boxes, boxes.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -432,9 +483,16 @@ int enqueue_link(fof_plan* h, const float* pos, cudaStream_t s)
     phase_begin(h, kPhBinScatter, s);
     FOF_TRY(launch_bin_scatter(pos, g, w, s));
     phase_end(h, kPhBinScatter, s);
+    FOF_TRY(cudaMemsetAsync(w.n_dense, 0, 4, s));
     phase_begin(h, kPhBrickSort, s);
-    FOF_TRY(launch_brick_sort(g, w, s));
+    FOF_TRY(launch_brick_sort(g, w, h->dense_min, s));
     phase_end(h, kPhBrickSort, s);
+    phase_begin(h, kPhDenseSelf, s);
+    FOF_TRY(launch_dense(g, w, h->dense_min, h->retry_cap, false, s));
+    phase_end(h, kPhDenseSelf, s);
+    phase_begin(h, kPhDensePairs, s);
+    FOF_TRY(launch_dense(g, w, h->dense_min, h->retry_cap, true, s));
+    phase_end(h, kPhDensePairs, s);
     phase_begin(h, kPhLink, s);
     FOF_TRY(launch_link(g, w, h->dense_min, h->retry_cap, s));
     phase_end(h, kPhLink, s);
@@ -542,7 +600,7 @@ size_t fof_batch_workspace_bytes(int32_t nbox, const double* box, const double* 
     int64_t tn, tb, tc;
     if (setup_batch(nbox, box, l_x, n, opt, boxes, tn, tb, tc) != FOF_OK)
         return 0;
-    return layout(nbox, tn, tb, tc).total;
+    return layout(nbox, tn, tb, tc, dense_min_of(opt)).total;
 }
 
 int fof_link(fof_handle h, const float* pos_dev, void* stream)
@@ -691,6 +749,26 @@ int fof_graph_launch(fof_handle h, void* stream)
             h->phase[k].launches += kPhaseLaunches[k];
         }
     }
+    return FOF_OK;
+}
+
+int fof_box_geometry(double box, double l_x, int64_t n, const fof_options* opt, fof_geometry* out)
+{
+    if (!out)
+        return FOF_ERR_ARG;
+    BoxDev b;
+    int rc = setup_box(box, l_x, n, opt, b);
+    if (rc != FOF_OK)
+        return rc;
+    out->cells_per_axis = b.nc;
+    out->brick_cells = b.r;
+    out->bricks_per_axis = b.nb;
+    out->sub_cells = b.q;
+    out->fine_per_axis = b.nf;
+    out->inv_fine = b.inv_hf;
+    out->xmax = b.xmax;
+    out->t_lo = b.t_lo;
+    out->t_hi = b.t_hi;
     return FOF_OK;
 }
 
@@ -875,6 +953,9 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
     w.parent = (int*)(ws + L.parent);
     w.minorig = (int*)(ws + L.minorig);
     w.cnt = (int*)(ws + L.cnt);
+    w.dense_list = (int64_t*)(ws + L.dense_list);
+    w.n_dense = (int*)(ws + L.n_dense);
+    w.dense_root = (int*)(ws + L.dense_root);
 
     // The array keeps the previous call's contents: the box table is
     // rewritten and every counter that must start at zero is cleared here.
@@ -887,10 +968,13 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
         FOF_TRY(cudaMemsetAsync(w.bcount, 0, 4 * (size_t)(tb + 1), s));
         FOF_TRY(cudaMemsetAsync(w.bcursor, 0, 4 * (size_t)(tb + 1), s));
         FOF_TRY(cudaMemsetAsync(w.tile_cnt, 0, 4 * (size_t)(w.n_tiles + 1), s));
+        FOF_TRY(cudaMemsetAsync(w.n_dense, 0, 4, s));
         FOF_TRY(launch_bin_count(pos_dev, g, w, s));
         FOF_TRY(launch_scan(w.bcount, w.bstart, tb, w.scan_tmp, w.scan_tmp_len, s));
         FOF_TRY(launch_bin_scatter(pos_dev, g, w, s));
-        FOF_TRY(launch_brick_sort(g, w, s));
+        FOF_TRY(launch_brick_sort(g, w, kDefaultDenseMin, s));
+        FOF_TRY(launch_dense(g, w, kDefaultDenseMin, kDefaultRetryCap, false, s));
+        FOF_TRY(launch_dense(g, w, kDefaultDenseMin, kDefaultRetryCap, true, s));
         FOF_TRY(launch_link(g, w, kDefaultDenseMin, kDefaultRetryCap, s));
         FOF_TRY(launch_finalize(g, w, s));
         FOF_TRY(launch_outputs(g, w, ids_dev, sizes_dev, min_size, s));

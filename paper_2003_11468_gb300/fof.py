@@ -40,6 +40,20 @@ class fof_options(ctypes.Structure):
     ]
 
 
+class fof_geometry(ctypes.Structure):
+    _fields_ = [
+        ("cells_per_axis", ctypes.c_int32),
+        ("brick_cells", ctypes.c_int32),
+        ("bricks_per_axis", ctypes.c_int32),
+        ("sub_cells", ctypes.c_int32),
+        ("fine_per_axis", ctypes.c_int32),
+        ("inv_fine", ctypes.c_float),
+        ("xmax", ctypes.c_float),
+        ("t_lo", ctypes.c_float),
+        ("t_hi", ctypes.c_float),
+    ]
+
+
 class FoFError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -77,6 +91,7 @@ def load():
             "fof_graph_build": ([P, P, P, P, P, i64, i32, P], ctypes.c_int),
             "fof_graph_launch": ([P, P], ctypes.c_int),
             "fof_plan_info": ([P, i32, P, P, P], ctypes.c_int),
+            "fof_box_geometry": ([f64, f64, i64, P, P], ctypes.c_int),
             "fof_set_timing": ([P, ctypes.c_int], ctypes.c_int),
             "fof_phase_times": ([P, P, P, P, ctypes.c_int], ctypes.c_int),
             "fof_reset_times": ([P], ctypes.c_int),
@@ -220,6 +235,13 @@ def fof_graph_build(h, pos, ids, sizes, catalogue, cat_capacity, min_size, strea
 
 def fof_graph_launch(h, stream) -> int:
     return _check(load().fof_graph_launch(h, _stream(stream)), "fof_graph_launch")
+
+
+def fof_box_geometry(box, l_x, n, opt: fof_options | None = None) -> fof_geometry:
+    out = fof_geometry()
+    _check(load().fof_box_geometry(box, l_x, n, ctypes.byref(opt) if opt is not None else None,
+                                   ctypes.byref(out)), "fof_box_geometry")
+    return out
 
 
 def fof_plan_info(h, b=0):
