@@ -1,0 +1,237 @@
+"""Continuous-batching Friends-of-Friends server over the C ABI.
+
+The paper runs FoF on-the-fly at fixed intervals of a simulation (Sec. 1)
+and its users analyse many snapshots; a GPU serving such jobs sees requests
+of very different sizes arriving at random times.  This server
+
+* queues requests as they arrive (`submit` returns a Future);
+* admits waiting requests, oldest first, while device memory (workspace from
+  `fof_batch_workspace_bytes` plus input/output buffers) fits the budget and
+  a slot (CUDA stream) is free; requests admitted together form one batch
+  plan (`fof_batch_create` with a caller-owned workspace), so small jobs share
+  one set of launches;
+* runs each batch on its slot's stream (H2D copy, `fof_link`,
+  `fof_groups_async`, D2H copy of ids, sizes and the catalogue), so batches
+  on different slots overlap on the device;
+* polls completion events, reads the status (`fof_result`), resolves the
+  futures, frees the memory and admits more work.
+
+Results are exactly those of a solo run (the partition is unique).  Memory
+comes from PyTorch's caching allocator, the only allocator used.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import fof
+
+
+@dataclass
+class Request:
+    pos: object                   # float32 [n, 3], host (pinned torch tensor or numpy)
+    box: float
+    l_x: float
+    min_size: int = 1
+    t_arrive: float = field(default_factory=time.perf_counter)
+    future: Future = field(default_factory=Future)
+
+
+@dataclass
+class Result:
+    ids: np.ndarray
+    sizes: np.ndarray
+    catalogue: np.ndarray         # [k, 2] (label, size), ascending label
+    n_groups: int
+    latency_s: float
+
+
+class _Batch:
+    def __init__(self, reqs, slot, stream, device):
+        import torch
+        self.reqs = reqs
+        self.slot = slot
+        self.stream = stream
+        ns = [r.pos.shape[0] for r in reqs]
+        self.ns = ns
+        self.total = int(sum(ns))
+        self.offsets = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        boxes = [r.box for r in reqs]
+        lxs = [r.l_x for r in reqs]
+        self.ws_bytes = fof.fof_batch_workspace_bytes(boxes, lxs, ns)
+        if self.ws_bytes == 0:
+            raise ValueError("invalid request geometry")
+        # one workspace + io block from the caching allocator
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        base = (self.ws.data_ptr() + 255) // 256 * 256
+        self.h = fof.fof_batch_create(boxes, lxs, ns, None, base, self.ws_bytes)
+        self.pos = torch.empty((max(self.total, 1), 3), dtype=torch.float32, device=device)
+        self.ids = torch.empty(max(self.total, 1), dtype=torch.int32, device=device)
+        self.sizes = torch.empty(max(self.total, 1), dtype=torch.int32, device=device)
+        self.cat = torch.empty((max(self.total, 1), 2), dtype=torch.int32, device=device)
+        self.ids_h = torch.empty(max(self.total, 1), dtype=torch.int32).pin_memory()
+        self.sizes_h = torch.empty(max(self.total, 1), dtype=torch.int32).pin_memory()
+        self.cat_h = torch.empty((max(self.total, 1), 2), dtype=torch.int32).pin_memory()
+        self.min_size = min(r.min_size for r in reqs)
+        self.event = torch.cuda.Event()
+
+    @staticmethod
+    def io_bytes(n):
+        return 12 * n + 8 * n + 8 * n
+
+    def launch(self):
+        import torch
+        with torch.cuda.stream(self.stream):
+            for r, o in zip(self.reqs, self.offsets[:-1]):
+                n = r.pos.shape[0]
+                if n:
+                    src = r.pos if hasattr(r.pos, "is_pinned") else torch.from_numpy(np.ascontiguousarray(r.pos))
+                    self.pos[o:o + n].copy_(src, non_blocking=True)
+            fof.fof_link(self.h, self.pos, self.stream)
+            fof.fof_groups_async(self.h, self.ids, self.sizes, self.cat, self.total, self.min_size,
+                                 self.stream)
+            self.ids_h.copy_(self.ids, non_blocking=True)
+            self.sizes_h.copy_(self.sizes, non_blocking=True)
+            self.cat_h.copy_(self.cat, non_blocking=True)
+            self.event.record(self.stream)
+
+    def finish(self):
+        code, ng, nk = fof.fof_result(self.h, len(self.reqs), self.stream)
+        now = time.perf_counter()
+        ids = self.ids_h.numpy()
+        sizes = self.sizes_h.numpy()
+        cat = self.cat_h.numpy()
+        k0 = 0
+        for i, r in enumerate(self.reqs):
+            o0, o1 = self.offsets[i], self.offsets[i + 1]
+            rows = cat[k0:k0 + nk[i]]
+            k0 += nk[i]
+            rows = rows[rows[:, 1] >= max(r.min_size, 1)].copy()
+            r.future.set_result(Result(ids[o0:o1].copy(), sizes[o0:o1].copy(), rows, ng[i],
+                                       now - r.t_arrive))
+        fof.fof_destroy(self.h)
+        self.h = None
+
+
+class Server:
+    """Continuous-batching FoF server on one GPU.
+
+    memory_budget: device bytes the server may hold for admitted work.
+    slots: concurrent batches (one CUDA stream each).
+    max_batch_boxes / max_batch_particles: limits of one batch plan.
+    """
+
+    def __init__(self, memory_budget: int = 120 << 30, slots: int = 4, max_batch_boxes: int = 64,
+                 max_batch_particles: int = 1 << 27, device: int = 0):
+        import torch
+        fof.load()
+        self.device = torch.device("cuda", device)
+        self.budget = int(memory_budget)
+        self.in_use = 0
+        self.max_boxes = max_batch_boxes
+        self.max_particles = max_batch_particles
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.free_slots = list(range(slots))
+        self.waiting = collections.deque()
+        self.running = []
+        self.lock = threading.Condition()
+        self.stop_flag = False
+        self.latencies = []
+        self.completed_particles = 0
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    # -- public ----------------------------------------------------------
+    def submit(self, pos, box: float, l_x: float, min_size: int = 1) -> Future:
+        req = Request(pos, float(box), float(l_x), int(min_size))
+        with self.lock:
+            self.waiting.append(req)
+            self.lock.notify()
+        return req.future
+
+    def close(self):
+        with self.lock:
+            self.stop_flag = True
+            self.lock.notify()
+        self.thread.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- scheduler -------------------------------------------------------
+    def _need_bytes(self, req):
+        n = req.pos.shape[0]
+        ws = fof.fof_batch_workspace_bytes([req.box], [req.l_x], [n])
+        return ws + _Batch.io_bytes(n) + 4096
+
+    def _admit(self):
+        """Form one batch from the head of the queue if memory and a slot allow."""
+        if not self.free_slots or not self.waiting:
+            return None
+        take, need, total = [], 0, 0
+        for req in self.waiting:
+            b = self._need_bytes(req)
+            n = req.pos.shape[0]
+            if take and (len(take) >= self.max_boxes or total + n > self.max_particles):
+                break
+            if self.in_use + need + b > self.budget:
+                break
+            take.append(req)
+            need += b
+            total += n
+        if not take:
+            if not self.running and self.waiting:
+                # a single request larger than the budget can never run
+                req = self.waiting.popleft()
+                req.future.set_exception(MemoryError("request exceeds the memory budget"))
+            return None
+        for _ in take:
+            self.waiting.popleft()
+        slot = self.free_slots.pop()
+        try:
+            batch = _Batch(take, slot, self.streams[slot], self.device)
+        except Exception as e:                      # geometry errors: fail those requests
+            self.free_slots.append(slot)
+            for r in take:
+                r.future.set_exception(e)
+            return None
+        batch.reserved = need
+        self.in_use += need
+        batch.launch()
+        return batch
+
+    def _loop(self):
+        import torch
+        torch.cuda.set_device(self.device)
+        while True:
+            with self.lock:
+                if self.stop_flag and not self.waiting and not self.running:
+                    return
+                while True:
+                    b = self._admit()
+                    if b is None:
+                        break
+                    self.running.append(b)
+                if not self.running and not self.waiting:
+                    self.lock.wait(timeout=0.05)
+                    continue
+            done = [b for b in self.running if b.event.query()]
+            for b in done:
+                b.finish()
+                with self.lock:
+                    self.running.remove(b)
+                    self.in_use -= b.reserved
+                    self.free_slots.append(b.slot)
+                    for r in b.reqs:
+                        self.latencies.append(r.future.result().latency_s)
+                    self.completed_particles += b.total
+            if not done:
+                time.sleep(0.0002)
