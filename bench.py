@@ -357,19 +357,174 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# batched and served forms against the plain per-box loop
+# ---------------------------------------------------------------------------
+
+def _clocks_start():
+    c = ClockSampler(0)
+    c.start()
+    time.sleep(0.3)
+    return c
+
+
+def run_batch(args):
+    """512 boxes (n log-uniform 16^3..160^3): one batch plan replayed as a CUDA
+    graph vs a loop of per-box plans, both timed with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2003_11468_gb300 import fof, synth
+    fof.load()
+    specs = synth.batch_512(args.boxes)
+    t0 = time.perf_counter()
+    poss = [synth.make_batch_box(sp) for sp in specs]
+    t_gen = time.perf_counter() - t0
+    ns = [sp["n"] for sp in specs]
+    total = int(sum(ns))
+    concat = torch.from_numpy(np.concatenate(poss)).cuda()
+    offs = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    stream = torch.cuda.Stream()
+    # batched: one plan, one graph
+    h = fof.fof_batch_create([sp["box"] for sp in specs], [sp["l_x"] for sp in specs], ns)
+    ids_b = torch.empty(total, dtype=torch.int32, device="cuda")
+    sizes_b = torch.empty_like(ids_b)
+    cat_b = torch.empty((total, 2), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    fof.fof_graph_build(h, concat, ids_b, sizes_b, cat_b, total, 20, stream)
+    for _ in range(args.warmup):
+        fof.fof_graph_launch(h, stream)
+        fof.fof_result(h, len(specs), stream)
+    clocks = _clocks_start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fof.fof_graph_launch(h, stream)
+    e1.record(stream)
+    code, ng, nk = fof.fof_result(h, len(specs), stream)
+    ms_batch = e0.elapsed_time(e1) / args.steps
+    # plain loop: a plan per box (created beforehand), link + groups per box
+    plans = [fof.fof_create(sp["box"], sp["l_x"], sp["n"]) for sp in specs]
+    ids_p = torch.empty(total, dtype=torch.int32, device="cuda")
+    sizes_p = torch.empty_like(ids_p)
+    cat_p = torch.empty((total, 2), dtype=torch.int32, device="cuda")
+
+    def loop():
+        for i, hp in enumerate(plans):
+            a, b = int(offs[i]), int(offs[i + 1])
+            fof.fof_link(hp, concat[a:b], stream)
+            fof.fof_groups(hp, ids_p[a:b], sizes_p[a:b], cat_p[a:b], b - a, 20, 1, stream)
+    for _ in range(args.warmup):
+        loop()
+    e0.record(stream)
+    for _ in range(args.steps):
+        loop()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    exact = bool(torch.equal(ids_b, ids_p)) and bool(torch.equal(sizes_b, sizes_p))
+    for hp in plans:
+        fof.fof_destroy(hp)
+    fof.fof_destroy(h)
+    line = {"metric": "particles grouped/s (batched, one CUDA graph)", "value": total / (ms_batch * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {len(specs)} clustered boxes", "particles": total,
+                       "status": code},
+            "plain_loop": {"value": total / (ms_plain * 1e-3), "unit": UNIT, "ms_per_step": ms_plain},
+            "speedup_vs_plain": ms_plain / ms_batch, "identical_to_plain": exact,
+            "gpu_launches": None, "clocks": clk, "gen_s": t_gen}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    """Poisson requests through the server vs the same requests one by one."""
+    import numpy as np
+    import torch
+    from paper_2003_11468_gb300 import fof, synth
+    from paper_2003_11468_gb300.server import Server
+    fof.load()
+    reqs = synth.served_requests(count=args.requests)
+    # a pool of distinct inputs, reused by the requests (bounded generation)
+    pool_n = sorted({int(np.exp(v)) for v in np.linspace(np.log(1e4), np.log(1e8), args.pool)})
+    t0 = time.perf_counter()
+    pool = {}
+    for k, n in enumerate(pool_n):
+        box = 100.0 * (n / 256 ** 3) ** (1.0 / 3.0)
+        pos = synth.clustered_box(n, box, max(1, int(round(20000 * n / 256 ** 3))), seed=5_000_000 + k)
+        pool[n] = (torch.from_numpy(pos).pin_memory(), box, synth.linking_length(n, box))
+    t_gen = time.perf_counter() - t0
+    keys = np.array(pool_n)
+    jobs = []
+    for r in reqs:
+        n = int(keys[np.argmin(np.abs(np.log(keys) - np.log(r["n"])))])
+        jobs.append((r["t_arrive"], n))
+    total = sum(n for _, n in jobs)
+    # plain: one request at a time, each with its own plan, results to host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _, n in jobs:
+        pos, box, l_x = pool[n]
+        with fof.FoF(box, l_x, n) as f:
+            ids, sizes, cat, _ = f.run(pos.cuda(non_blocking=True), min_size=20)
+            ids.cpu(), sizes.cpu(), cat.cpu()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    # served: Poisson arrivals replayed in real time
+    clocks = _clocks_start()
+    nmax = max(pool_n)
+    _, bmax, lmax = pool[nmax]
+    with Server(memory_budget=args.budget_gb << 30, slots=args.slots, prealloc=(bmax, lmax, nmax)) as srv:
+        futs = []
+        start = time.perf_counter()
+        for t_arr, n in jobs:
+            wait = start + t_arr - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            pos, box, l_x = pool[n]
+            futs.append(srv.submit(pos, box, l_x, 20))
+        for f in futs:
+            f.result()
+        t_served = time.perf_counter() - start
+    lat = np.array(srv.latencies)
+    clk = clocks.stop()
+    line = {"metric": "particles grouped/s (served, Poisson 200/s)", "value": total / t_served, "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": t_served * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{len(jobs)} Poisson requests, n log-uniform 1e4..1e8",
+                       "particles": total, "budget_gb": args.budget_gb, "slots": args.slots},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                           "p99": float(np.percentile(lat, 99) * 1e3)},
+            "plain_loop": {"value": total / t_plain, "unit": UNIT, "seconds": t_plain},
+            "clocks": clk, "gen_s": t_gen}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="1024", choices=["1024", "256", "32k"])
+    ap.add_argument("--workload", default="1024", choices=["1024", "256", "32k", "batch", "served"])
+    ap.add_argument("--boxes", type=int, default=512, help="batch workload: number of boxes")
+    ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
+    ap.add_argument("--pool", type=int, default=24, help="served workload: distinct inputs")
+    ap.add_argument("--slots", type=int, default=2)
+    ap.add_argument("--budget-gb", type=int, default=120)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-k", type=int, default=8, help="CPU sample is a 1/k^3 volume box")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_gpu(args)
 
 

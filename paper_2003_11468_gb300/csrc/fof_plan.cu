@@ -201,6 +201,56 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
     return FOF_OK;
 }
 
+// Pinned status blocks come from one process-wide slab cut into 4 KB
+// chunks, so creating and destroying plans never calls cudaMallocHost /
+// cudaFreeHost (the latter waits for the whole device).  Plans whose block
+// is larger than a chunk (batches of more than 250 boxes) allocate their own.
+constexpr size_t kPinChunk = 4096;
+constexpr int kPinChunks = 1024;
+std::mutex g_pin_mu;
+char* g_pin_slab = nullptr;
+bool g_pin_used[kPinChunks];
+
+char* pinned_alloc(size_t bytes, bool& from_slab)
+{
+    from_slab = false;
+    if (bytes <= kPinChunk) {
+        std::lock_guard<std::mutex> lock(g_pin_mu);
+        if (!g_pin_slab) {
+            if (cudaHostAlloc((void**)&g_pin_slab, kPinChunk * kPinChunks, cudaHostAllocPortable) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                g_pin_slab = nullptr;
+            }
+        }
+        if (g_pin_slab)
+            for (int k = 0; k < kPinChunks; ++k)
+                if (!g_pin_used[k]) {
+                    g_pin_used[k] = true;
+                    from_slab = true;
+                    return g_pin_slab + k * kPinChunk;
+                }
+    }
+    char* p = nullptr;
+    if (cudaMallocHost((void**)&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pinned_free(char* p, bool from_slab)
+{
+    if (!p)
+        return;
+    if (from_slab) {
+        std::lock_guard<std::mutex> lock(g_pin_mu);
+        g_pin_used[(p - g_pin_slab) / kPinChunk] = false;
+    } else {
+        cudaFreeHost(p);
+    }
+}
+
 struct PhaseTimer {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool pending = false;
@@ -221,6 +271,7 @@ struct fof_plan {
     bool own_ws = false;
     char* results_dev = nullptr;
     char* results_host = nullptr;   // pinned
+    bool results_from_slab = false;
     ResultsLayout rl{};
     int dense_min = kDefaultDenseMin;
     int retry_cap = kDefaultRetryCap;
@@ -399,8 +450,8 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
         h->own_ws = true;
     }
     h->ws_bytes = L.total;
-    if (cudaMallocHost((void**)&h->results_host, h->rl.bytes) != cudaSuccess) {
-        cudaGetLastError();
+    h->results_host = pinned_alloc(h->rl.bytes, h->results_from_slab);
+    if (!h->results_host) {
         fof_destroy(h);
         return FOF_ERR_OOM;
     }
@@ -837,7 +888,7 @@ void fof_destroy(fof_handle h)
     if (h->sizes_d) cudaFree(h->sizes_d);
     if (h->cat_d) cudaFree(h->cat_d);
     if (h->own_ws && h->ws) cudaFree(h->ws);
-    if (h->results_host) cudaFreeHost(h->results_host);
+    pinned_free(h->results_host, h->results_from_slab);
     delete h;
 }
 

@@ -9,12 +9,13 @@ of very different sizes arriving at random times.  This server
   `fof_batch_workspace_bytes` plus input/output buffers) fits the budget and
   a slot (CUDA stream) is free; requests admitted together form one batch
   plan (`fof_batch_create` with a caller-owned workspace), so small jobs share
-  one set of launches;
+  one set of launches; each slot keeps its device and pinned host buffers
+  and only grows them, so steady-state serving allocates nothing;
 * runs each batch on its slot's stream (H2D copy, `fof_link`,
   `fof_groups_async`, D2H copy of ids, sizes and the catalogue), so batches
   on different slots overlap on the device;
 * polls completion events, reads the status (`fof_result`), resolves the
-  futures, frees the memory and admits more work.
+  futures, returns the batch's share of the budget and admits more work.
 
 Results are exactly those of a solo run (the partition is unique).  Memory
 comes from PyTorch's caching allocator, the only allocator used.
@@ -51,9 +52,41 @@ class Result:
     latency_s: float
 
 
-class _Batch:
-    def __init__(self, reqs, slot, stream, device):
+class _SlotBuffers:
+    """Device and pinned host buffers of one slot, grown on demand and kept,
+    so that steady-state serving allocates nothing."""
+
+    def __init__(self, device):
+        self.device = device
+        self.cap_ws = 0
+        self.cap_n = 0
+        self.ws = self.pos = self.ids = self.sizes = self.cat = None
+        self.ids_h = self.sizes_h = None
+
+    def ensure(self, ws_bytes, total):
         import torch
+        if ws_bytes > self.cap_ws:
+            self.ws = None
+            self.cap_ws = int(ws_bytes * 1.25) + 4096
+            self.ws = torch.empty(self.cap_ws + 256, dtype=torch.uint8, device=self.device)
+        n = max(total, 1)
+        if n > self.cap_n:
+            self.pos = self.ids = self.sizes = self.cat = self.ids_h = self.sizes_h = None
+            self.cap_n = int(n * 1.25) + 1024
+            c = self.cap_n
+            self.pos = torch.empty((c, 3), dtype=torch.float32, device=self.device)
+            self.ids = torch.empty(c, dtype=torch.int32, device=self.device)
+            self.sizes = torch.empty(c, dtype=torch.int32, device=self.device)
+            self.cat = torch.empty((c, 2), dtype=torch.int32, device=self.device)
+            self.ids_h = torch.empty(c, dtype=torch.int32).pin_memory()
+            self.sizes_h = torch.empty(c, dtype=torch.int32).pin_memory()
+
+    def ws_ptr(self):
+        return (self.ws.data_ptr() + 255) // 256 * 256
+
+
+class _Batch:
+    def __init__(self, reqs, slot, stream, bufs: _SlotBuffers):
         self.reqs = reqs
         self.slot = slot
         self.stream = stream
@@ -66,18 +99,11 @@ class _Batch:
         self.ws_bytes = fof.fof_batch_workspace_bytes(boxes, lxs, ns)
         if self.ws_bytes == 0:
             raise ValueError("invalid request geometry")
-        # one workspace + io block from the caching allocator
-        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
-        base = (self.ws.data_ptr() + 255) // 256 * 256
-        self.h = fof.fof_batch_create(boxes, lxs, ns, None, base, self.ws_bytes)
-        self.pos = torch.empty((max(self.total, 1), 3), dtype=torch.float32, device=device)
-        self.ids = torch.empty(max(self.total, 1), dtype=torch.int32, device=device)
-        self.sizes = torch.empty(max(self.total, 1), dtype=torch.int32, device=device)
-        self.cat = torch.empty((max(self.total, 1), 2), dtype=torch.int32, device=device)
-        self.ids_h = torch.empty(max(self.total, 1), dtype=torch.int32).pin_memory()
-        self.sizes_h = torch.empty(max(self.total, 1), dtype=torch.int32).pin_memory()
-        self.cat_h = torch.empty((max(self.total, 1), 2), dtype=torch.int32).pin_memory()
+        bufs.ensure(self.ws_bytes, self.total)
+        self.b = bufs
+        self.h = fof.fof_batch_create(boxes, lxs, ns, None, bufs.ws_ptr(), self.ws_bytes)
         self.min_size = min(r.min_size for r in reqs)
+        import torch
         self.event = torch.cuda.Event()
 
     @staticmethod
@@ -86,26 +112,26 @@ class _Batch:
 
     def launch(self):
         import torch
+        b, t = self.b, self.total
         with torch.cuda.stream(self.stream):
             for r, o in zip(self.reqs, self.offsets[:-1]):
                 n = r.pos.shape[0]
                 if n:
                     src = r.pos if hasattr(r.pos, "is_pinned") else torch.from_numpy(np.ascontiguousarray(r.pos))
-                    self.pos[o:o + n].copy_(src, non_blocking=True)
-            fof.fof_link(self.h, self.pos, self.stream)
-            fof.fof_groups_async(self.h, self.ids, self.sizes, self.cat, self.total, self.min_size,
-                                 self.stream)
-            self.ids_h.copy_(self.ids, non_blocking=True)
-            self.sizes_h.copy_(self.sizes, non_blocking=True)
-            self.cat_h.copy_(self.cat, non_blocking=True)
+                    b.pos[o:o + n].copy_(src, non_blocking=True)
+            fof.fof_link(self.h, b.pos, self.stream)
+            fof.fof_groups_async(self.h, b.ids, b.sizes, b.cat, t, self.min_size, self.stream)
+            b.ids_h[:t].copy_(b.ids[:t], non_blocking=True)
+            b.sizes_h[:t].copy_(b.sizes[:t], non_blocking=True)
             self.event.record(self.stream)
 
     def finish(self):
         code, ng, nk = fof.fof_result(self.h, len(self.reqs), self.stream)
+        b = self.b
+        ids = b.ids_h.numpy()
+        sizes = b.sizes_h.numpy()
+        cat = b.cat[: int(sum(nk))].cpu().numpy()     # only the rows that exist
         now = time.perf_counter()
-        ids = self.ids_h.numpy()
-        sizes = self.sizes_h.numpy()
-        cat = self.cat_h.numpy()
         k0 = 0
         for i, r in enumerate(self.reqs):
             o0, o1 = self.offsets[i], self.offsets[i + 1]
@@ -124,10 +150,12 @@ class Server:
     memory_budget: device bytes the server may hold for admitted work.
     slots: concurrent batches (one CUDA stream each).
     max_batch_boxes / max_batch_particles: limits of one batch plan.
+    prealloc: optional (box, l_x, n) of the largest batch expected; every
+    slot's buffers are sized for it up front.
     """
 
-    def __init__(self, memory_budget: int = 120 << 30, slots: int = 4, max_batch_boxes: int = 64,
-                 max_batch_particles: int = 1 << 27, device: int = 0):
+    def __init__(self, memory_budget: int = 120 << 30, slots: int = 2, max_batch_boxes: int = 64,
+                 max_batch_particles: int = 1 << 27, device: int = 0, prealloc=None):
         import torch
         fof.load()
         self.device = torch.device("cuda", device)
@@ -136,6 +164,13 @@ class Server:
         self.max_boxes = max_batch_boxes
         self.max_particles = max_batch_particles
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.buffers = [_SlotBuffers(self.device) for _ in range(slots)]
+        if prealloc is not None:
+            # (box, l_x, n) of the largest expected batch: size every slot now
+            box, l_x, n = prealloc
+            ws = fof.fof_batch_workspace_bytes([box], [l_x], [n])
+            for b in self.buffers:
+                b.ensure(ws, n)
         self.free_slots = list(range(slots))
         self.waiting = collections.deque()
         self.running = []
@@ -197,7 +232,7 @@ class Server:
             self.waiting.popleft()
         slot = self.free_slots.pop()
         try:
-            batch = _Batch(take, slot, self.streams[slot], self.device)
+            batch = _Batch(take, slot, self.streams[slot], self.buffers[slot])
         except Exception as e:                      # geometry errors: fail those requests
             self.free_slots.append(slot)
             for r in take:
