@@ -197,11 +197,15 @@ int fof_graph_launch(fof_handle h, void *stream);
  * inv_fine = float32(nc*q / box), so a coordinate's fine index is
  * min(nc*q - 1, (int)(x * inv_fine)) with a float32 multiply and its cell
  * index is the fine one divided by q; xmax = largest valid coordinate;
- * t_lo / t_hi = float32 squared-distance bounds of the pre-test.
+ * t_lo / t_hi = float32 squared-distance bounds of the pre-test; bb_reach2
+ * bounds the float32 squared gap between a particle and the bounding box of
+ * particles it can link to.
  * Returns FOF_OK or FOF_ERR_ARG (same rules as fof_create_ex). */
 typedef struct {
     int32_t cells_per_axis, brick_cells, bricks_per_axis, sub_cells, fine_per_axis;
     float inv_fine, xmax, t_lo, t_hi;
+    float bb_reach2;   /* squared float32 gap from a bounding box of particles
+                          beyond which no particle has a partner */
 } fof_geometry;
 
 int fof_box_geometry(double box, double l_x, int64_t n, const fof_options *opt, fof_geometry *out);

@@ -48,6 +48,8 @@ struct BoxDev {
     float reach2;     // (l_x / hf)^2 (1 + 2^-6): a sub-cell whose box is farther
                       // than this (in fine units, squared) holds no partner
     int32_t team_min; // occupancy from which k_link links a cell as a warp team
+    float bb_reach2;  // (l_x + 8 L 2^-24)^2 (1 + 2^-20): squared float32 gap from a
+                      // bounding box beyond which no partner lies
 };
 
 // A cell is "subdivided" (linked by the dense kernels) when its box splits
@@ -289,6 +291,7 @@ struct Work {
     int64_t scan_tmp_len;
     int* tile_cnt;      // [n_tiles + 1] catalogue entries per label tile
     int* tile_off;      // [n_tiles + 1]
+    int* out_cursor;    // [total_n / kOutChunk + 1] fill of each output bucket
     int64_t n_tiles;
     Status* status;     // device status
     unsigned long long* n_groups;  // [nbox]
@@ -300,6 +303,8 @@ struct Work {
 };
 
 constexpr int kCatTile = 2048;  // labels per catalogue tile
+constexpr int kOutChunkLog = 12;                 // outputs: input indices per chunk
+constexpr int kOutChunk = 1 << kOutChunkLog;
 
 int sm_count();
 

@@ -69,17 +69,15 @@ __device__ __forceinline__ unsigned reach_mask(const float4& p, const BoxDev& b,
     const int lx = fine_coord(p.x, b) - c.cx * q;
     const int ly = fine_coord(p.y, b) - c.cy * q;
     const int lz = fine_coord(p.z, b) - c.cz * q;
-    const bool hx = lx >= q - 2, hy = ly >= q - 2, hz = lz >= q - 2;
-    const bool wx = lx <= 1, wy = ly <= 1;
-    unsigned m = 0;
-    for (int k = 0; k < 13; ++k) {
-        int dx, dy, dz;
-        fwd_offset(k, dx, dy, dz);
-        bool ok = (dx == 0 || (dx > 0 ? hx : wx)) && (dy == 0 || (dy > 0 ? hy : wy)) &&
-                  (dz == 0 || hz);            // dz is never negative in the half stencil
-        m |= (unsigned)ok << k;
-    }
-    return m;
+    const unsigned hx = lx >= q - 2, hy = ly >= q - 2, hz = lz >= q - 2;
+    const unsigned wx = lx <= 1, wy = ly <= 1;
+    // per axis, bit d+1 set when offset d in {-1, 0, +1} is reachable
+    const unsigned xm = wx | 2u | (hx << 2);
+    const unsigned ym = wy | 2u | (hy << 2);
+    // k = 0..8: dz = +1, k = 3 (dy+1) + (dx+1); k = 9..11: dz = 0, dy = +1;
+    // k = 12: dz = dy = 0, dx = +1  (the order of fwd_offset)
+    unsigned m9 = ((ym & 1u) ? xm : 0u) | ((ym & 2u) ? xm << 3 : 0u) | ((ym & 4u) ? xm << 6 : 0u);
+    return (hz ? m9 : 0u) | (hy ? xm << 9 : 0u) | (hx << 12);
 }
 
 __device__ __forceinline__ float4 shfl4(float4 v, int src)
@@ -90,33 +88,66 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src)
     return v;
 }
 
-// One warp links the lanes in `peers` (all in cell `self` of box b) against
+// Bounding box of the team's particles.
+struct TeamBox {
+    float lx, ly, lz, hx, hy, hz;
+};
+
+__device__ __forceinline__ float warp_min(float v)
+{
+    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// One warp links the lanes with `act` (all in one cell of box b) against
 // the candidates in [j0, j1).  `own` = the candidates lie in the own cell,
-// so lane i only takes j > its slot.
+// so lane i only takes j > its slot.  Otherwise (filter = true) a candidate
+// farther than bb_reach2 (squared, float32) from the team's bounding box,
+// after the periodic shift (sx, sy, sz) of its cell, is dropped before any
+// root lookup: bb_reach2 covers l_x plus the float32 rounding of the shift
+// and of the gap (setup_box), so no linked pair is dropped.
 __device__ __forceinline__ void team_link(int* __restrict__ parent, const float4* __restrict__ sorted,
-                                          const BoxDev& b, bool mine, int64_t s, const float4& p,
-                                          int& ri, int j0, int j1, bool own, int cap, int* err)
+                                          const BoxDev& b, bool act, int64_t s, const float4& p,
+                                          int& ri, int j0, int j1, bool own, bool filter,
+                                          const TeamBox& tb, float sx, float sy, float sz, int cap,
+                                          int* err)
 {
     const int lane = threadIdx.x & 31;
+    const int ref_lane = __ffs(__ballot_sync(kFull, act)) - 1;
     for (int jb = j0; jb < j1; jb += kWarp) {
         int j = jb + lane;
         bool jv = j < j1;
         float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        int rj = -1;
         if (jv) {
             q = sorted[j];
-            rj = uf_find(parent, j, err);
+            if (filter) {
+                float x = q.x + sx, y = q.y + sy, z = q.z + sz;
+                float gx = fmaxf(0.f, fmaxf(tb.lx - x, x - tb.hx));
+                float gy = fmaxf(0.f, fmaxf(tb.ly - y, y - tb.hy));
+                float gz = fmaxf(0.f, fmaxf(tb.lz - z, z - tb.hz));
+                jv = gx * gx + gy * gy + gz * gz <= b.bb_reach2;
+            }
         }
-        // chunk skip: every root on both sides equal to one value
-        int ref = __shfl_sync(kFull, mine ? ri : rj, __ffs(__ballot_sync(kFull, mine)) - 1);
-        bool agree = (!mine || ri == ref) && (!jv || rj == ref);
-        if (__all_sync(kFull, agree))
+        unsigned cand = __ballot_sync(kFull, jv);
+        if (!cand)
             continue;
-        int kmax = j1 - jb < kWarp ? j1 - jb : kWarp;
-        for (int t = 0; t < kmax; ++t) {
-            int rt = __shfl_sync(kFull, rj, t);
-            float4 qt = shfl4(q, t);
-            bool need = mine && ri != rt && (!own || jb + t > s);
+        const int rj = jv ? uf_find(parent, j, err) : -1;
+        // chunk skip: every root on both sides equal to one value
+        const int ref = __shfl_sync(kFull, ri, ref_lane);
+        if (__all_sync(kFull, (!act || ri == ref) && (!jv || rj == ref)))
+            continue;
+        while (cand) {
+            const int t = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const int rt = __shfl_sync(kFull, rj, t);
+            const float4 qt = shfl4(q, t);
+            const bool need = act && ri != rt && (!own || jb + t > s);
             if (!__any_sync(kFull, need))
                 continue;
             if (need && linked(p, qt, b))
@@ -170,11 +201,20 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
             tc.cy = __shfl_sync(kFull, c.cy, lead);
             tc.cz = __shfl_sync(kFull, c.cz, lead);
             int ri = mine ? uf_find(parent, (int)s, err) : -1;
+            const float inf = __int_as_float(0x7f800000);
+            TeamBox tbx;
+            tbx.lx = warp_min(mine ? p.x : inf);
+            tbx.ly = warp_min(mine ? p.y : inf);
+            tbx.lz = warp_min(mine ? p.z : inf);
+            tbx.hx = warp_max(mine ? p.x : -inf);
+            tbx.hy = warp_max(mine ? p.y : -inf);
+            tbx.hz = warp_max(mine ? p.z : -inf);
             // own cell: partners after the first lane of the team
             {
                 int first = (int)__shfl_sync(kFull, s, lead);
                 int end = __shfl_sync(kFull, c1, lead);
-                team_link(parent, sorted, b, mine, s, p, ri, first + 1, end, true, cap, err);
+                team_link(parent, sorted, b, mine, s, p, ri, first + 1, end, true, false, tbx, 0.f,
+                          0.f, 0.f, cap, err);
             }
             const unsigned reach = mine ? reach_mask(p, b, tc) : 0u;
             const unsigned team_reach = __reduce_or_sync(kFull, reach);
@@ -183,10 +223,16 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
                     continue;
                 int64_t nk = nbr_key(b, tc, k);
                 int j0 = cell_start[nk], j1 = cell_start[nk + 1];
-                if (is_sub(j1 - j0, b, dense_min))
+                if (j1 == j0 || is_sub(j1 - j0, b, dense_min))
                     continue;
+                int dx, dy, dz;
+                fwd_offset(k, dx, dy, dz);
+                // periodic shift that puts the neighbour's particles next to the team
+                const float sx = tc.cx + dx < 0 ? -b.Lf : (tc.cx + dx >= b.nc ? b.Lf : 0.f);
+                const float sy = tc.cy + dy < 0 ? -b.Lf : (tc.cy + dy >= b.nc ? b.Lf : 0.f);
+                const float sz = tc.cz + dz >= b.nc ? b.Lf : 0.f;
                 team_link(parent, sorted, b, mine && ((reach >> k) & 1u), s, p, ri, j0, j1, false,
-                          cap, err);
+                          b.nc >= 3, tbx, sx, sy, sz, cap, err);
             }
         }
 

@@ -8,8 +8,8 @@
 //              with the atomic additions of its parallel size count
 //              (Sec. 3.4.1) aggregated per warp.
 //   outputs    ids[i] = smallest index of i's group; sizes[label] = size,
-//              0 elsewhere; per-box group counts; catalogue entries counted
-//              per label tile.
+//              0 elsewhere (two passes, see below); per-box group counts;
+//              catalogue entries counted per label tile.
 //   catalogue  prefix sum over the label tiles, then each tile writes its
 //              (label, size) entries in ascending label order.
 #include "fof_internal.cuh"
@@ -60,14 +60,27 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t total, int* __restrict
     }
 }
 
-__global__ void __launch_bounds__(256) k_outputs(Geometry g, const float4* __restrict__ sorted,
-                                                 const int* __restrict__ parent,
-                                                 const int* __restrict__ minorig,
-                                                 const int* __restrict__ cnt,
-                                                 int32_t* __restrict__ ids, int32_t* __restrict__ sizes,
-                                                 int32_t thr, unsigned long long* __restrict__ n_groups,
-                                                 unsigned long long* __restrict__ n_cat,
-                                                 int* __restrict__ tile_cnt)
+// Outputs go back to input order in two passes, so that no 4-byte value
+// is written to a random address (a read-modify-write of a whole sector):
+//   bucket  for every binned slot: label and size of its group, and one
+//           (offset, value) pair appended to the bucket of its input index's
+//           chunk of kOutChunk indices.  A chunk holds exactly kOutChunk
+//           inputs (the last one fewer), so bucket c starts at c*kOutChunk
+//           with no prefix sum, and the ~n/kOutChunk write heads stay in L2.
+//   place   one CTA per chunk: the pairs are placed in shared memory and
+//           ids and sizes written out coalesced.
+// A pair is (offset | is_label << 31, value): value = size when the input
+// is its group's label (then the label is the input's own box-local
+// index), else the label.
+__global__ void __launch_bounds__(256) k_outputs_bucket(Geometry g, const float4* __restrict__ sorted,
+                                                        const int* __restrict__ parent,
+                                                        const int* __restrict__ minorig,
+                                                        const int* __restrict__ cnt, int32_t thr,
+                                                        unsigned long long* __restrict__ n_groups,
+                                                        unsigned long long* __restrict__ n_cat,
+                                                        int* __restrict__ tile_cnt,
+                                                        int* __restrict__ out_cursor,
+                                                        int2* __restrict__ pairs, int* __restrict__ err)
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -81,23 +94,69 @@ __global__ void __launch_bounds__(256) k_outputs(Geometry g, const float4* __res
         int64_t p0 = g.boxes[bi].p0;
         int root = parent[s];
         int label = minorig[root];
-        int size = cnt[root];
         int o = __float_as_int(sorted[s].w);
-        ids[p0 + o] = label;
-        sizes[p0 + o] = (o == label) ? size : 0;
+        bool is_label = o == label;
+        int size = is_label || root == (int)s ? cnt[root] : 0;
+        int64_t gidx = p0 + o;
+        int chunk = (int)(gidx >> kOutChunkLog);
+        unsigned peers = __match_any_sync(active, chunk);
+        int leader = __ffs(peers) - 1;
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        int off = 0;
+        if (lane == leader)
+            off = atomicAdd(out_cursor + chunk, __popc(peers));
+        off = __shfl_sync(active, off, leader) + rank;
+        if (off < kOutChunk) {
+            int word0 = (int)(gidx & (kOutChunk - 1)) | (is_label ? (int)0x80000000u : 0);
+            pairs[((int64_t)chunk << kOutChunkLog) + off] = make_int2(word0, is_label ? size : label);
+        } else {
+            atomicOr(err, kErrInternal);
+        }
         bool is_root = root == (int)s;
         bool in_cat = is_root && size >= thr;
         // per-box counts, aggregated over lanes of the same box
-        unsigned peers = __match_any_sync(active, bi);
-        int leader = __ffs(peers) - 1;
-        int ng = __popc(__ballot_sync(active, is_root) & peers);
-        int nk = __popc(__ballot_sync(active, in_cat) & peers);
-        if (lane == leader) {
+        unsigned bpeers = __match_any_sync(active, bi);
+        int bleader = __ffs(bpeers) - 1;
+        int ng = __popc(__ballot_sync(active, is_root) & bpeers);
+        int nk = __popc(__ballot_sync(active, in_cat) & bpeers);
+        if (lane == bleader) {
             if (ng) atomicAdd(n_groups + bi, (unsigned long long)ng);
             if (nk) atomicAdd(n_cat + bi, (unsigned long long)nk);
         }
         if (in_cat)
             atomicAdd(tile_cnt + (p0 + label) / kCatTile, 1);
+    }
+}
+
+__global__ void __launch_bounds__(512) k_outputs_place(Geometry g, const int2* __restrict__ pairs,
+                                                       int32_t* __restrict__ ids,
+                                                       int32_t* __restrict__ sizes)
+{
+    __shared__ int s_ids[kOutChunk];
+    __shared__ int s_sizes[kOutChunk];
+    const int64_t n_chunks = (g.total_n + kOutChunk - 1) >> kOutChunkLog;
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const int64_t base = c << kOutChunkLog;
+        const int len = (int)min((int64_t)kOutChunk, g.total_n - base);
+        for (int k = threadIdx.x; k < len; k += blockDim.x) {
+            int2 e = pairs[base + k];
+            int off = e.x & (kOutChunk - 1);
+            if (e.x < 0) {                       // the input is its group's label
+                int64_t gidx = base + off;
+                int bi = box_of(g.box_p0, g.nbox, gidx);
+                s_ids[off] = (int)(gidx - g.boxes[bi].p0);
+                s_sizes[off] = e.y;
+            } else {
+                s_ids[off] = e.y;
+                s_sizes[off] = 0;
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < len; k += blockDim.x) {
+            ids[base + k] = s_ids[k];
+            sizes[base + k] = s_sizes[k];
+        }
+        __syncthreads();
     }
 }
 
@@ -194,8 +253,13 @@ cudaError_t launch_outputs(const Geometry& g, const Work& w, int32_t* ids, int32
     if (g.total_n == 0)
         return cudaSuccess;
     int32_t thr = min_size < 1 ? 1 : min_size;
-    k_outputs<<<grid_for(g.total_n, 256, 8), 256, 0, s>>>(g, w.sorted, w.parent, w.minorig, w.cnt, ids,
-                                                        sizes, thr, w.n_groups, w.n_cat, w.tile_cnt);
+    int2* pairs = (int2*)w.tmp;            // the brick-order copy is dead by now
+    k_outputs_bucket<<<grid_for(g.total_n, 256, 8), 256, 0, s>>>(
+        g, w.sorted, w.parent, w.minorig, w.cnt, thr, w.n_groups, w.n_cat, w.tile_cnt, w.out_cursor,
+        pairs, &w.status->err);
+    int64_t n_chunks = (g.total_n + kOutChunk - 1) >> kOutChunkLog;
+    int blocks = (int)(n_chunks < (int64_t)sm_count() * 4 ? n_chunks : (int64_t)sm_count() * 4);
+    k_outputs_place<<<blocks, 512, 0, s>>>(g, pairs, ids, sizes);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ const char* kPhaseNames[kNumPhases] = {
     "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "dense_self", "dense_pairs", "link",
     "finalize", "outputs", "catalogue",
 };
-const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 1, 1, 1, 1, 1, 4};
+const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 1, 1, 1, 1, 2, 4};
 
 constexpr int64_t kMaxTotal = 2147483646LL;   // slots and labels are int32
 constexpr int kDefaultRetryCap = 1 << 20;
@@ -186,6 +186,16 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
         b.reach2 = (float)(rf * rf * (1.0 + std::ldexp(1.0, -20)));
     }
     b.team_min = (o && o->reserved[0] > 0) ? o->reserved[0] : kDefaultTeamMin;
+    // Team bounding-box filter.  A neighbour particle shifted by +-float32(L)
+    // and the float32 gaps to the box are each within L 2^-24 (shift: the
+    // sum and float32(L); gap: one subtraction) per axis, 3 L 2^-24 together,
+    // sqrt(3) * 3 < 5.2 over three axes; a partner is at most l_x (1 + 2^-50)
+    // away; so a linked pair has squared gap below (l_x + 8 L 2^-24)^2, and
+    // the final 2^-20 covers the rounding of the squares and their sum.
+    {
+        double rb = l_x * (1.0 + std::ldexp(1.0, -50)) + 8.0 * L * std::ldexp(1.0, -24);
+        b.bb_reach2 = float_up(rb * rb * (1.0 + std::ldexp(1.0, -20)));
+    }
     b.xmax = (float)L;
     while ((double)b.xmax >= L) b.xmax = std::nextafter(b.xmax, 0.0f);
 
@@ -297,7 +307,8 @@ namespace {
 
 struct Layout {
     size_t boxes, p0, brick0, results, bcount, bstart, bcursor, scan_tmp, tile_cnt, tile_off,
-        cell_start, tmp, sorted, parent, minorig, cnt, dense_list, n_dense, dense_root, total;
+        cell_start, tmp, sorted, parent, minorig, cnt, dense_list, n_dense, dense_root, out_cursor,
+        total;
     int64_t scan_len, n_tiles, dense_cap;
 };
 
@@ -334,6 +345,7 @@ Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cel
     L.dense_list = take(8 * (size_t)L.dense_cap);
     L.n_dense = take(4);
     L.dense_root = take(4 * (size_t)(total_n / dense_min + 2));
+    L.out_cursor = take(4 * (size_t)((total_n >> kOutChunkLog) + 2));
     L.total = off;
     return L;
 }
@@ -500,6 +512,7 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     w.dense_list = (int64_t*)(ws + L.dense_list);
     w.n_dense = (int*)(ws + L.n_dense);
     w.dense_root = (int*)(ws + L.dense_root);
+    w.out_cursor = (int*)(ws + L.out_cursor);
 
     cudaError_t e = cudaMemcpy(ws + L.boxes, boxes.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -561,6 +574,7 @@ int enqueue_groups(fof_plan* h, int32_t* ids, int32_t* sizes, fof_group* cat, in
         FOF_TRY(cudaMemsetAsync(h->results_dev + h->rl.groups_off, 0,
                                 h->rl.bytes - h->rl.groups_off, s));
         FOF_TRY(cudaMemsetAsync(w.tile_cnt, 0, 4 * (size_t)(w.n_tiles + 1), s));
+        FOF_TRY(cudaMemsetAsync(w.out_cursor, 0, 4 * (size_t)((g.total_n >> kOutChunkLog) + 2), s));
         phase_begin(h, kPhFinalize, s);
         FOF_TRY(launch_finalize(g, w, s));
         phase_end(h, kPhFinalize, s);
@@ -820,6 +834,7 @@ int fof_box_geometry(double box, double l_x, int64_t n, const fof_options* opt, 
     out->xmax = b.xmax;
     out->t_lo = b.t_lo;
     out->t_hi = b.t_hi;
+    out->bb_reach2 = b.bb_reach2;
     return FOF_OK;
 }
 
@@ -1007,6 +1022,7 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
     w.dense_list = (int64_t*)(ws + L.dense_list);
     w.n_dense = (int*)(ws + L.n_dense);
     w.dense_root = (int*)(ws + L.dense_root);
+    w.out_cursor = (int*)(ws + L.out_cursor);
 
     // The array keeps the previous call's contents: the box table is
     // rewritten and every counter that must start at zero is cleared here.
@@ -1020,6 +1036,7 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
         FOF_TRY(cudaMemsetAsync(w.bcursor, 0, 4 * (size_t)(tb + 1), s));
         FOF_TRY(cudaMemsetAsync(w.tile_cnt, 0, 4 * (size_t)(w.n_tiles + 1), s));
         FOF_TRY(cudaMemsetAsync(w.n_dense, 0, 4, s));
+        FOF_TRY(cudaMemsetAsync(w.out_cursor, 0, 4 * (size_t)((n >> kOutChunkLog) + 2), s));
         FOF_TRY(launch_bin_count(pos_dev, g, w, s));
         FOF_TRY(launch_scan(w.bcount, w.bstart, tb, w.scan_tmp, w.scan_tmp_len, s));
         FOF_TRY(launch_bin_scatter(pos_dev, g, w, s));

@@ -51,6 +51,7 @@ class fof_geometry(ctypes.Structure):
         ("xmax", ctypes.c_float),
         ("t_lo", ctypes.c_float),
         ("t_hi", ctypes.c_float),
+        ("bb_reach2", ctypes.c_float),
     ]
 
 

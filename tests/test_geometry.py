@@ -129,6 +129,34 @@ def test_float32_pretest_never_contradicts_exact(case):
     assert band.mean() < 0.01
 
 
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_bounding_box_gap_keeps_every_partner(case):
+    """The team filter drops a candidate when its float32 gap to the box of
+    the team's particles exceeds bb_reach2; replay it with one-particle boxes
+    (the tightest case) and periodic shifts by float32(L)."""
+    box, l_x, n = CASES[case]
+    gm = fof.fof_box_geometry(box, l_x, n)
+    rng = np.random.default_rng(300 + case)
+    a, b = _pairs(rng, box, l_x, 300000, 0.98, 1.0001)
+    # put a near the low faces so the partner often sits across the wrap
+    a = (a.astype(np.float64) * 0.01).astype(f32)
+    d = rng.normal(size=a.shape)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    b = np.mod(a.astype(np.float64) + d * (l_x * rng.uniform(0.98, 1.0001, size=(a.shape[0], 1))), box)
+    b = b.astype(f32)
+    b[b >= f32(box)] = 0
+    link = oracle.linked_many(a, b, box, l_x)
+    a, b = a[link], b[link]
+    Lf = f32(box)
+    # the shift that brings b next to a (as the kernel's cell offsets do)
+    shift = np.where(b - a > Lf / 2, -Lf, np.where(a - b > Lf / 2, Lf, f32(0))).astype(f32)
+    x = (b + shift).astype(f32)
+    gap = np.abs(x - a).astype(f32)
+    g2 = (gap[:, 0] * gap[:, 0] + gap[:, 1] * gap[:, 1] + gap[:, 2] * gap[:, 2]).astype(f32)
+    assert link.sum() > 1000
+    assert (g2 <= f32(gm.bb_reach2)).all()
+
+
 def test_valid_coordinate_limit():
     for box, l_x, n in CASES:
         gm = fof.fof_box_geometry(box, l_x, n)
