@@ -88,6 +88,27 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src)
     return v;
 }
 
+// Unions found in one chunk, done lane-parallel: `links` holds, per lane,
+// the candidates (lane indices of the chunk) it is linked to; every round
+// each lane with a pending link merges with that candidate's root snapshot
+// `rj`, so the chunk waits for as many union latencies as its busiest lane
+// has links, not one per linked candidate.  A snapshot root equal to the
+// lane's current or last merged root needs nothing (groups only merge).
+__device__ __forceinline__ void chunk_unions(int* parent, unsigned links, int rj, int& ri, int& last,
+                                             int cap, int* err)
+{
+    while (__any_sync(kFull, links != 0u)) {
+        const bool has = links != 0u;
+        const int u = has ? __ffs(links) - 1 : 0;
+        links &= links - 1u;
+        const int rt = __shfl_sync(kFull, rj, u);
+        if (has && rt != ri && rt != last) {
+            ri = uf_union(parent, ri, rt, cap, err);
+            last = rt;
+        }
+    }
+}
+
 // Bounding box of the team's particles.
 struct TeamBox {
     float lx, ly, lz, hx, hy, hz;
@@ -114,7 +135,7 @@ __device__ __forceinline__ float warp_max(float v)
 // and of the gap (setup_box), so no linked pair is dropped.
 __device__ __forceinline__ void team_link(int* __restrict__ parent, const float4* __restrict__ sorted,
                                           const BoxDev& b, bool act, int64_t s, const float4& p,
-                                          int& ri, int j0, int j1, bool own, bool filter,
+                                          int& ri, int& last, int j0, int j1, bool own, bool filter,
                                           const TeamBox& tb, float sx, float sy, float sz, int cap,
                                           int* err)
 {
@@ -142,17 +163,94 @@ __device__ __forceinline__ void team_link(int* __restrict__ parent, const float4
         const int ref = __shfl_sync(kFull, ri, ref_lane);
         if (__all_sync(kFull, (!act || ri == ref) && (!jv || rj == ref)))
             continue;
+        unsigned links = 0u;
         while (cand) {
             const int t = __ffs(cand) - 1;
             cand &= cand - 1;
             const int rt = __shfl_sync(kFull, rj, t);
             const float4 qt = shfl4(q, t);
-            const bool need = act && ri != rt && (!own || jb + t > s);
+            // rt == last: this lane already merged with that group
+            const bool need = act && ri != rt && rt != last && (!own || jb + t > s);
             if (!__any_sync(kFull, need))
                 continue;
             if (need && linked(p, qt, b))
-                ri = uf_union(parent, ri, rt, cap, err);
+                links |= 1u << t;
         }
+        chunk_unions(parent, links, rj, ri, last, cap, err);
+    }
+}
+
+// The reachable forward neighbours of a team's cell as ONE stream of
+// candidates, 32 per step: lane k < 13 holds neighbour k's first slot (j0k)
+// and the number of its particles to visit (cntk, 0 when the team does not
+// reach it).  Each candidate keeps its neighbour index, which gives its
+// periodic shift for the box filter and the lanes that reach it.
+__device__ __forceinline__ void team_stream(int* __restrict__ parent, const float4* __restrict__ sorted,
+                                            const BoxDev& b, bool mine, unsigned reach, const float4& p,
+                                            int& ri, int& last, const Cell& tc, int j0k, int cntk,
+                                            const TeamBox& tb, bool filter, int cap, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    int x = cntk;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    const int start_k = x - cntk;
+    const int total = __shfl_sync(kFull, x, 31);
+    const int ref_lane = __ffs(__ballot_sync(kFull, mine)) - 1;
+    for (int base = 0; base < total; base += kWarp) {
+        const int t = base + lane;
+        bool jv = t < total;
+        int lo = 0, hi = 12;                   // last neighbour whose stream starts at or before t
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            int mid = (lo + hi + 1) >> 1;
+            int sm = __shfl_sync(kFull, start_k, mid);
+            if (lo < hi) {
+                if (sm <= t) lo = mid; else hi = mid - 1;
+            }
+        }
+        const int k = lo;
+        const int j = __shfl_sync(kFull, j0k, k) + (t - __shfl_sync(kFull, start_k, k));
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jv) {
+            q = sorted[j];
+            if (filter) {
+                int dx, dy, dz;
+                fwd_offset(k, dx, dy, dz);
+                const float sx = tc.cx + dx < 0 ? -b.Lf : (tc.cx + dx >= b.nc ? b.Lf : 0.f);
+                const float sy = tc.cy + dy < 0 ? -b.Lf : (tc.cy + dy >= b.nc ? b.Lf : 0.f);
+                const float sz = tc.cz + dz >= b.nc ? b.Lf : 0.f;
+                const float xx = q.x + sx, yy = q.y + sy, zz = q.z + sz;
+                const float gx = fmaxf(0.f, fmaxf(tb.lx - xx, xx - tb.hx));
+                const float gy = fmaxf(0.f, fmaxf(tb.ly - yy, yy - tb.hy));
+                const float gz = fmaxf(0.f, fmaxf(tb.lz - zz, zz - tb.hz));
+                jv = gx * gx + gy * gy + gz * gz <= b.bb_reach2;
+            }
+        }
+        unsigned cand = __ballot_sync(kFull, jv);
+        if (!cand)
+            continue;
+        const int rj = jv ? uf_find(parent, j, err) : -1;
+        const int ref = __shfl_sync(kFull, ri, ref_lane);
+        if (__all_sync(kFull, (!mine || ri == ref) && (!jv || rj == ref)))
+            continue;
+        unsigned links = 0u;
+        while (cand) {
+            const int u = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const int rt = __shfl_sync(kFull, rj, u);
+            const int kt = __shfl_sync(kFull, k, u);
+            const float4 qt = shfl4(q, u);
+            // rt == last: this lane already merged with that group
+            const bool need = mine && ((reach >> kt) & 1u) && ri != rt && rt != last;
+            if (!__any_sync(kFull, need))
+                continue;
+            if (need && linked(p, qt, b))
+                links |= 1u << u;
+        }
+        chunk_unions(parent, links, rj, ri, last, cap, err);
     }
 }
 
@@ -201,6 +299,7 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
             tc.cy = __shfl_sync(kFull, c.cy, lead);
             tc.cz = __shfl_sync(kFull, c.cz, lead);
             int ri = mine ? uf_find(parent, (int)s, err) : -1;
+            int last = -1;                    // root snapshot of this lane's last union
             const float inf = __int_as_float(0x7f800000);
             TeamBox tbx;
             tbx.lx = warp_min(mine ? p.x : inf);
@@ -213,27 +312,24 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
             {
                 int first = (int)__shfl_sync(kFull, s, lead);
                 int end = __shfl_sync(kFull, c1, lead);
-                team_link(parent, sorted, b, mine, s, p, ri, first + 1, end, true, false, tbx, 0.f,
+                team_link(parent, sorted, b, mine, s, p, ri, last, first + 1, end, true, false, tbx, 0.f,
                           0.f, 0.f, cap, err);
             }
             const unsigned reach = mine ? reach_mask(p, b, tc) : 0u;
             const unsigned team_reach = __reduce_or_sync(kFull, reach);
-            for (int k = 0; k < 13; ++k) {
-                if (!((team_reach >> k) & 1u) || nbr_duplicate(b, tc, k, key))
-                    continue;
-                int64_t nk = nbr_key(b, tc, k);
+            // lane k < 13: neighbour k's range, if the team reaches it and
+            // the dense kernels do not own it
+            int j0k = 0, cntk = 0;
+            if (lane < 13 && ((team_reach >> lane) & 1u) && !nbr_duplicate(b, tc, lane, key)) {
+                int64_t nk = nbr_key(b, tc, lane);
                 int j0 = cell_start[nk], j1 = cell_start[nk + 1];
-                if (j1 == j0 || is_sub(j1 - j0, b, dense_min))
-                    continue;
-                int dx, dy, dz;
-                fwd_offset(k, dx, dy, dz);
-                // periodic shift that puts the neighbour's particles next to the team
-                const float sx = tc.cx + dx < 0 ? -b.Lf : (tc.cx + dx >= b.nc ? b.Lf : 0.f);
-                const float sy = tc.cy + dy < 0 ? -b.Lf : (tc.cy + dy >= b.nc ? b.Lf : 0.f);
-                const float sz = tc.cz + dz >= b.nc ? b.Lf : 0.f;
-                team_link(parent, sorted, b, mine && ((reach >> k) & 1u), s, p, ri, j0, j1, false,
-                          b.nc >= 3, tbx, sx, sy, sz, cap, err);
+                if (j1 > j0 && !is_sub(j1 - j0, b, dense_min)) {
+                    j0k = j0;
+                    cntk = j1 - j0;
+                }
             }
+            team_stream(parent, sorted, b, mine, reach, p, ri, last, tc, j0k, cntk, tbx, b.nc >= 3, cap,
+                        err);
         }
 
         // ---- sparse cells: every lane on its own ----
