@@ -88,7 +88,7 @@ typedef struct {
                                 (default 256)                                */
     int32_t retry_cap;       /* max CAS attempts per union (default 2^20)    */
     int32_t reserved[4];     /* [0]: occupancy from which a warp links a cell
-                                as a team (default 8); others must be 0      */
+                                as a team (default 4); others must be 0      */
 } fof_options;
 
 /* ---------------------------------------------------------------------- */

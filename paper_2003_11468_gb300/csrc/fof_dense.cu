@@ -47,12 +47,13 @@ struct DenseSmem {
     int* nbpref;         // [27] prefix of the neighbour particle counts to visit
     int* nbflag;         // [26] per neighbour: 1 = both cells single groups
     int* nbdone;         // [26] per neighbour: a link was made (single groups)
+    unsigned* rowmask;   // [kMaxQ * kMaxQ] per (z, y) row: bit x = sub-cell non-empty
 };
 
 __host__ __device__ constexpr size_t dense_smem_bytes()
 {
     return (size_t)kDenseMax * (16 + 4 + 2 + 2) + (size_t)(kMaxQ3 + 1) * 4 + (size_t)kMaxQ3 * 4 +
-           (size_t)kMaxQ3 * 2 + 512;
+           (size_t)kMaxQ3 * 2 + 512 + (size_t)kMaxQ * kMaxQ * 4;
 }
 
 __device__ DenseSmem carve(unsigned char* base)
@@ -69,6 +70,7 @@ __device__ DenseSmem carve(unsigned char* base)
     s.nbflag = s.misc + 72;
     s.nbdone = s.misc + 100;
     off += 512;
+    s.rowmask = (unsigned*)(base + off);   off += (size_t)kMaxQ * kMaxQ * 4;
     s.skey = (unsigned short*)(base + off); off += (size_t)kDenseMax * 2;
     s.order = (unsigned short*)(base + off); off += (size_t)kDenseMax * 2;
     s.ne = (unsigned short*)(base + off);
@@ -172,6 +174,14 @@ __device__ int build_cell(const DenseSmem& S, const float4* __restrict__ sorted,
             S.ne[slot] = (unsigned short)a;
         }
     }
+    for (int row = threadIdx.x; row < q * q; row += blockDim.x) {
+        unsigned mask = 0;
+        for (int x = 0; x < q; ++x) {
+            int a = row * q + x;
+            mask |= (unsigned)(S.sstart[a + 1] > S.sstart[a]) << x;
+        }
+        S.rowmask[row] = mask;
+    }
     __syncthreads();
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         int pos = atomicAdd(S.groot + S.skey[k], 1);
@@ -199,12 +209,16 @@ __device__ __forceinline__ int link_window(const DenseSmem& S, int* parent, cons
     const float ux = __fmul_rn(pj.x, b.inv_hf) - (float)fine_coord(pj.x, b);
     const float uy = __fmul_rn(pj.y, b.inv_hf) - (float)fine_coord(pj.y, b);
     const float uz = __fmul_rn(pj.z, b.inv_hf) - (float)fine_coord(pj.z, b);
+    const unsigned span = (x1 >= x0) ? ((2u << x1) - (1u << x0)) : 0u;   // bits x0..x1
     for (int z = z0; z <= z1; ++z) {
         // gap from pj to the sub-cell layer z, in fine units (0 when adjacent)
         float gz = z < rz ? (float)(rz - z - 1) + uz : (z > rz ? (float)(z - rz - 1) + (1.f - uz) : 0.f);
         for (int y = y0; y <= y1; ++y) {
             float gy = y < ry ? (float)(ry - y - 1) + uy : (y > ry ? (float)(y - ry - 1) + (1.f - uy) : 0.f);
-            for (int x = x0; x <= x1; ++x) {
+            unsigned bits = S.rowmask[z * q + y] & span;     // non-empty sub-cells only
+            while (bits) {
+                const int x = __ffs(bits) - 1;
+                bits &= bits - 1u;
                 float gx = x < rx ? (float)(rx - x - 1) + ux : (x > rx ? (float)(x - rx - 1) + (1.f - ux) : 0.f);
                 if (gx * gx + gy * gy + gz * gz > b.reach2)
                     continue;                    // the whole sub-cell is out of reach
@@ -316,39 +330,54 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_self(Geometry g, Work w
         // three face offsets first; when they leave the cell one group the
         // other 59 offsets cannot change anything and are skipped
         for (int pass = 0; pass < 2; ++pass) {
-            const int nofs = pass == 0 ? 3 : 62;
+            // pass 0: the 3 face offsets (one item each); pass 1: the 13
+            // half-stencil rows (dz, dy) of the +-2 stencil, each a span of
+            // dx, whose non-empty sub-cells come from the row masks
+            const int nofs = pass == 0 ? 3 : 13;
             for (int item = threadIdx.x; item < ne * nofs; item += blockDim.x) {
-                int a = S.ne[item / nofs];
-                int o = item % nofs;
-                int dx, dy, dz;
+                const int a = S.ne[item / nofs];
+                const int o = item % nofs;
+                const int ax = a % q, ay = (a / q) % q, az = a / (q * q);
+                int dy, dz, dxlo, dxhi;
                 if (pass == 0) {
-                    dx = o == 0; dy = o == 1; dz = o == 2;
-                } else {
-                    half_offset2(o, dx, dy, dz);
-                    if (dx + dy + dz == 1 && dx >= 0 && dy >= 0 && dz >= 0)
-                        continue;                   // a face offset, done in pass 0
+                    dz = o == 2; dy = o == 1; dxlo = dxhi = o == 0;
+                } else if (o < 10) {             // dz = 1, 2 and dy = -2..2
+                    dz = 1 + o / 5; dy = o % 5 - 2; dxlo = -2; dxhi = 2;
+                } else if (o < 12) {             // dz = 0, dy = 1, 2
+                    dz = 0; dy = o - 9; dxlo = -2; dxhi = 2;
+                } else {                         // dz = dy = 0, dx = 1, 2
+                    dz = 0; dy = 0; dxlo = 1; dxhi = 2;
                 }
-                int ax = a % q, ay = (a / q) % q, az = a / (q * q);
-                int bx = ax + dx, by = ay + dy, bz = az + dz;
-                if (bx < 0 || bx >= q || by < 0 || by >= q || bz < 0 || bz >= q)
+                const int by = ay + dy, bz = az + dz;
+                if (by < 0 || by >= q || bz >= q)
                     continue;
-                int bb = (bz * q + by) * q + bx;
-                int b0 = S.sstart[bb], b1 = S.sstart[bb + 1];
-                if (b0 == b1)
+                const int xlo = max(ax + dxlo, 0), xhi = min(ax + dxhi, q - 1);
+                if (xlo > xhi)
                     continue;
-                int ra = lfind(S.lpar, S.groot[a], err), rb = lfind(S.lpar, S.groot[bb], err);
-                if (ra == rb)
-                    continue;
-                int a0 = S.sstart[a], a1 = S.sstart[a + 1];
-                bool done = false;
-                for (int u = a0; u < a1 && !done; ++u) {
-                    float4 pu = S.P[S.order[u]];
-                    for (int v = b0; v < b1; ++v)
-                        if (linked(pu, S.P[S.order[v]], b)) {
-                            lunion(S.lpar, ra, rb, err);
-                            done = true;
-                            break;
-                        }
+                unsigned bits = S.rowmask[bz * q + by] & ((2u << xhi) - (1u << xlo));
+                while (bits) {
+                    const int bx = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    if (pass == 1 && ((bx - ax == 1 && dy == 0 && dz == 0) ||
+                                      (bx == ax && dy == 1 && dz == 0) ||
+                                      (bx == ax && dy == 0 && dz == 1)))
+                        continue;                // a face offset, done in pass 0
+                    const int bb = (bz * q + by) * q + bx;
+                    int ra = lfind(S.lpar, S.groot[a], err), rb = lfind(S.lpar, S.groot[bb], err);
+                    if (ra == rb)
+                        continue;
+                    const int a0 = S.sstart[a], a1 = S.sstart[a + 1];
+                    const int b0 = S.sstart[bb], b1 = S.sstart[bb + 1];
+                    bool done = false;
+                    for (int u = a0; u < a1 && !done; ++u) {
+                        float4 pu = S.P[S.order[u]];
+                        for (int v = b0; v < b1; ++v)
+                            if (linked(pu, S.P[S.order[v]], b)) {
+                                lunion(S.lpar, ra, rb, err);
+                                done = true;
+                                break;
+                            }
+                    }
                 }
             }
             __syncthreads();
