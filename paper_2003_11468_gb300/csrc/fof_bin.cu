@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
                                                              int* __restrict__ err,
                                                              int64_t* __restrict__ dense_list,
                                                              int* __restrict__ n_dense,
-                                                             int dense_min)
+                                                             int dense_min,
+                                                             int64_t* __restrict__ team_list,
+                                                             int* __restrict__ n_team)
 {
     __shared__ int hist[kMaxR3];
     __shared__ int sw[32];
@@ -232,12 +234,15 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
         int ex = block_exclusive_scan(run, sw, total);
         const int64_t cbase = b.cell0 + (gb - b.brick0) * (int64_t)r3;
         for (int c = c0; c < c0 + per && c < r3; ++c) {
-            int h = hist[c];
+            const int h = hist[c];
+            const int start = s0 + ex;
             hist[c] = ex;                       // becomes the cursor
-            cell_start[cbase + c] = s0 + ex;
+            cell_start[cbase + c] = start;
             ex += h;
             if (is_sub(h, b, dense_min))
                 dense_list[atomicAdd(n_dense, 1)] = cbase + c;
+            else if (h >= b.team_min && h <= kTeamSelfMax)
+                team_list[atomicAdd(n_team, 1)] = ((int64_t)h << 32) | (uint32_t)start;
         }
         __syncthreads();
         for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
@@ -318,7 +323,7 @@ cudaError_t launch_brick_sort(const Geometry& g, const Work& w, int dense_min, c
     k_brick_sort<<<(unsigned)blocks, kSortThreads, 0, s>>>(g, w.tmp, w.bstart, w.sorted, w.parent,
                                                          w.minorig, w.cnt, w.cell_start,
                                                          &w.status->err, w.dense_list, w.n_dense,
-                                                         dense_min);
+                                                         dense_min, w.team_list, w.n_team);
     return cudaGetLastError();
 }
 

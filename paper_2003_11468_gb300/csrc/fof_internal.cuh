@@ -55,6 +55,9 @@ struct BoxDev {
 // A cell is "subdivided" (linked by the dense kernels) when its box splits
 // cells (q > 1) and it holds between dense_min and kDenseMax particles.
 constexpr int kDenseMax = 3072;   // particles of a subdivided cell (shared memory)
+// Largest team cell whose own pairs one warp links in shared memory
+// (k_team_self); larger unsplit cells link their own pairs in k_link.
+constexpr int kTeamSelfMax = 256;
 constexpr int kMaxQ = 12;
 constexpr int kMaxQ3 = kMaxQ * kMaxQ * kMaxQ;
 
@@ -183,7 +186,7 @@ __device__ __forceinline__ double wrap64(double d, double L)
 
 // Exact predicate: s = (dx*dx + dy*dy) + dz*dz in IEEE double with every
 // operation rounded to nearest and no contraction; linked iff s <= l2.
-static __device__ __noinline__ bool linked_exact(float4 p, float4 q, double L, double l2)
+__device__ __forceinline__ bool linked_exact_inl(const float4& p, const float4& q, double L, double l2)
 {
     double dx = wrap64(__dsub_rn((double)p.x, (double)q.x), L);
     double dy = wrap64(__dsub_rn((double)p.y, (double)q.y), L);
@@ -191,6 +194,12 @@ static __device__ __noinline__ bool linked_exact(float4 p, float4 q, double L, d
     double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
     s = __dadd_rn(s, __dmul_rn(dz, dz));
     return s <= l2;
+}
+
+// Out of line where register pressure matters: the band is rarely entered.
+static __device__ __noinline__ bool linked_exact(float4 p, float4 q, double L, double l2)
+{
+    return linked_exact_inl(p, q, L, l2);
 }
 
 // Pre-test in float32, exact test only inside the uncertainty band.
@@ -300,6 +309,9 @@ struct Work {
     int* n_dense;        // number of entries in dense_list
     int* dense_root;     // [total_n / dense_min + 1] by first slot / dense_min:
                          // root of a subdivided cell that is one group, else -1
+    int64_t* team_list;  // [team_cap] team cells (team_min..kTeamSelfMax particles, not
+                         // subdivided): size << 32 | first slot
+    int* n_team;         // number of entries in team_list
 };
 
 constexpr int kCatTile = 2048;  // labels per catalogue tile
@@ -319,6 +331,7 @@ cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, int re
 size_t dense_smem();
 cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, int retry_cap,
                         cudaStream_t s);
+cudaError_t launch_team_self(const Geometry& g, const Work& w, cudaStream_t s);
 cudaError_t launch_finalize(const Geometry& g, const Work& w, cudaStream_t s);
 cudaError_t launch_outputs(const Geometry& g, const Work& w, int32_t* ids, int32_t* sizes,
                            int32_t min_size, cudaStream_t s);

@@ -308,12 +308,13 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
             tbx.hx = warp_max(mine ? p.x : -inf);
             tbx.hy = warp_max(mine ? p.y : -inf);
             tbx.hz = warp_max(mine ? p.z : -inf);
-            // own cell: partners after the first lane of the team
+            // own cell: linked by k_team_self unless the cell is larger
             {
                 int first = (int)__shfl_sync(kFull, s, lead);
                 int end = __shfl_sync(kFull, c1, lead);
-                team_link(parent, sorted, b, mine, s, p, ri, last, first + 1, end, true, false, tbx, 0.f,
-                          0.f, 0.f, cap, err);
+                if (end - __shfl_sync(kFull, c0, lead) > kTeamSelfMax)
+                    team_link(parent, sorted, b, mine, s, p, ri, last, first + 1, end, true, false, tbx, 0.f,
+                              0.f, 0.f, cap, err);
             }
             const unsigned reach = mine ? reach_mask(p, b, tc) : 0u;
             const unsigned team_reach = __reduce_or_sync(kFull, reach);
@@ -354,7 +355,234 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
     }
 }
 
+// Self task of a team cell (team_min..kTeamSelfMax particles, not split
+// into sub-cells), one warp per cell.  The cell's particles are staged in
+// shared memory; the adjacency of the cell is built as bit rows, one
+// 32 x 32 block at a time: lane i tests (i, j) for the 32 j of a block,
+// collecting row i's word, and a ballot over the lanes gives row j's word of
+// the mirrored block, so each unordered pair is tested once outside the
+// diagonal blocks.  The components are then traced by breadth-first search
+// over bit sets (frontier rows OR-reduced across the warp), in ascending
+// order of their smallest member s, and every member's parent is set to s.
+// Isolated particles keep parent = self.  The kernel runs before any kernel
+// that links across cells, so no other thread touches these parents.
+constexpr int kTeamWarps = 4;
+constexpr int kTeamMax = kTeamSelfMax;
+constexpr int kTeamWords = kTeamMax / 32;
+constexpr int kAdjStride = kTeamWords + 1;          // odd stride: conflict-free rows
+
+struct TeamSmem {
+    float4 P[kTeamMax];
+    unsigned adj[kTeamMax * kAdjStride];
+};
+
+size_t team_smem_bytes()
+{
+    return sizeof(TeamSmem) * kTeamWarps;
+}
+
+// Positions that link to nothing: rows and columns beyond the cell's
+// particles.  Any difference with a real position or the other sentinel
+// squares to +inf in float32, so the pre-test rejects it.
+constexpr float kFar = 1e30f;
+
+// Tests of lane i's particle against particles jb*32 + t, t < jn8 (a
+// multiple of 8), returning row i's word of block jb.  For an off-diagonal
+// block (kOff) the ballot of each test is row j's word of block ib and is
+// stored by lane 0.  Inside one cell no pair needs the periodic wrap when
+// the box has at least 3 cells per axis (the cell side is then below L/2,
+// so the wrapped float32 separation equals the plain difference); kWrap
+// takes the full predicate for boxes with fewer cells.
+template <bool kOff, bool kWrap>
+__device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem& S, int jb, int ib, int jn8,
+                                                int lane, const BoxDev& b)
+{
+    const float4* pj = &S.P[jb * 32];
+    unsigned* colp = &S.adj[jb * 32 * kAdjStride + ib];
+    unsigned row = 0;
+    for (int t0 = 0; t0 < jn8; t0 += 8) {
+        unsigned byte = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float4 q = pj[t0 + u];
+            bool lk;
+            if (kWrap) {
+                const float s2 = d2_f32(pi, q, b.Lf);
+                lk = s2 <= b.t_hi;
+                if (lk && !(s2 < b.t_lo))
+                    lk = linked_exact_inl(pi, q, b.L, b.l2);
+            } else {
+                const float dx = __fsub_rn(pi.x, q.x);
+                const float dy = __fsub_rn(pi.y, q.y);
+                const float dz = __fsub_rn(pi.z, q.z);
+                const float s2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                lk = s2 <= b.t_hi;
+                if (lk && !(s2 < b.t_lo))
+                    lk = linked_exact_inl(pi, q, b.L, b.l2);
+            }
+            byte |= (unsigned)lk << u;
+            if (kOff) {
+                const unsigned c = __ballot_sync(kFull, lk);
+                if (lane == 0)
+                    colp[(t0 + u) * kAdjStride] = c;
+            }
+        }
+        row |= byte << t0;
+    }
+    return row;
+}
+
+// Positions of a listed cell (size << 32 | first slot) into registers:
+// lane k holds particles k, k + 32, ...
+__device__ __forceinline__ void team_fetch(float4 (&R)[kTeamWords], int64_t e, const float4* __restrict__ sorted,
+                                           int lane)
+{
+    const int c0 = (int)(uint32_t)e, m = min((int)(e >> 32), kTeamMax);
+#pragma unroll
+    for (int r = 0; r < kTeamWords; ++r)
+        if (lane + 32 * r < m)
+            R[r] = sorted[c0 + lane + 32 * r];
+}
+
+__global__ void __launch_bounds__(kTeamWarps * 32, 4) k_team_self(Geometry g, const int64_t* __restrict__ list,
+                                                              const int* __restrict__ n_list,
+                                                              const float4* __restrict__ sorted,
+                                                              int* __restrict__ parent, int* err)
+{
+    extern __shared__ float4 team_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    TeamSmem& S = reinterpret_cast<TeamSmem*>(team_raw)[wid];
+    const int n = *n_list;
+    const int stride = gridDim.x * kTeamWarps;
+    // software pipeline: the next cell's positions are loaded into
+    // registers while this cell is linked, and the entry after it is read
+    int it = blockIdx.x * kTeamWarps + wid;
+    int64_t e = it < n ? list[it] : 0;
+    float4 R[kTeamWords];
+    team_fetch(R, e, sorted, lane);
+    int64_t e_next = it + stride < n ? list[it + stride] : 0;
+    for (; it < n; it += stride) {
+        const int c0 = (int)(uint32_t)e, m = (int)(e >> 32);
+        const int nw = (m + 31) >> 5;
+        if (m <= kTeamMax) {
+#pragma unroll
+            for (int r = 0; r < kTeamWords; ++r) {   // the ragged tail links nothing
+                const int k = lane + 32 * r;
+                if (k < nw * 32)
+                    S.P[k] = k < m ? R[r] : make_float4(kFar, kFar, kFar, 0.f);
+            }
+        }
+        __syncwarp();
+        e = e_next;
+        if (it + stride < n)
+            team_fetch(R, e, sorted, lane);
+        e_next = it + 2 * stride < n ? list[it + 2 * stride] : 0;
+        if (m > kTeamMax) {                    // not a team cell: the list is inconsistent
+            if (lane == 0) atomicOr(err, kErrInternal);
+            continue;
+        }
+        const BoxDev& b = g.boxes[box_of(g.box_p0, g.nbox, c0)];
+
+        // adjacency rows
+        for (int ib = 0; ib < nw; ++ib) {
+            const int i = ib * 32 + lane;
+            const float4 pi = i < m ? S.P[i] : make_float4(-kFar, -kFar, -kFar, 0.f);
+            for (int jb = ib; jb < nw; ++jb) {
+                const int jn8 = (min(32, m - jb * 32) + 7) & ~7;
+                unsigned row;
+                if (b.nc >= 3) {
+                    row = jb == ib ? block_tests<false, false>(pi, S, jb, ib, jn8, lane, b)
+                                   : block_tests<true, false>(pi, S, jb, ib, jn8, lane, b);
+                } else {
+                    row = jb == ib ? block_tests<false, true>(pi, S, jb, ib, jn8, lane, b)
+                                   : block_tests<true, true>(pi, S, jb, ib, jn8, lane, b);
+                }
+                if (jb == ib)
+                    row &= ~(1u << lane);      // the particle itself
+                if (i < m)
+                    S.adj[i * kAdjStride + jb] = row;
+            }
+        }
+        __syncwarp();
+
+        // lane w < nw holds word w of each vertex set
+        unsigned todo = 0;
+        for (int ib = 0; ib < nw; ++ib) {
+            const int v = ib * 32 + lane;
+            unsigned any = 0;
+            if (v < m)
+                for (int k = 0; k < nw; ++k)
+                    any |= S.adj[v * kAdjStride + k];
+            const unsigned w = __ballot_sync(kFull, any != 0);
+            todo = lane == ib ? w : todo;
+        }
+        for (;;) {
+            const unsigned nz = __ballot_sync(kFull, todo != 0);
+            if (!nz)
+                break;
+            const int w0 = __ffs(nz) - 1;
+            const int s = w0 * 32 + __ffs(__shfl_sync(kFull, todo, w0)) - 1;
+            unsigned comp = lane == w0 ? 1u << (s & 31) : 0u;
+            unsigned front = comp;
+            for (int step = 0; step < kTeamMax; ++step) {   // every step adds a vertex
+                unsigned acc[kTeamWords];
+#pragma unroll
+                for (int k = 0; k < kTeamWords; ++k)
+                    acc[k] = 0;
+                for (int w = 0; w < nw; ++w) {
+                    const unsigned fw = __shfl_sync(kFull, front, w);
+                    if ((fw >> lane) & 1u) {
+                        const unsigned* r = &S.adj[(w * 32 + lane) * kAdjStride];
+#pragma unroll
+                        for (int k = 0; k < kTeamWords; ++k)
+                            if (k < nw) acc[k] |= r[k];
+                    }
+                }
+                unsigned nxt = 0;
+#pragma unroll
+                for (int k = 0; k < kTeamWords; ++k)
+                    if (k < nw) {
+                        const unsigned r = __reduce_or_sync(kFull, acc[k]);
+                        nxt = lane == k ? r : nxt;
+                    }
+                nxt &= ~comp;
+                comp |= nxt;
+                front = nxt;
+                if (!__ballot_sync(kFull, nxt != 0))
+                    break;
+            }
+            todo &= ~comp;
+            for (int w = 0; w < nw; ++w) {
+                const unsigned cw = __shfl_sync(kFull, comp, w);
+                if ((cw >> lane) & 1u)
+                    parent[c0 + w * 32 + lane] = c0 + s;
+            }
+        }
+        __syncwarp();                          // smem reused by the next cell
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_team_self(const Geometry& g, const Work& w, cudaStream_t s)
+{
+    if (g.total_n == 0)
+        return cudaSuccess;
+    // the shared-memory opt-in is per device; setting it again is harmless
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        e = cudaFuncSetAttribute(k_team_self, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)team_smem_bytes());
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) configured[dev] = true;
+    }
+    k_team_self<<<sm_count() * 4, kTeamWarps * 32, team_smem_bytes(), s>>>(
+        g, w.team_list, w.n_team, w.sorted, w.parent, &w.status->err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, int retry_cap, cudaStream_t s)
 {

@@ -37,21 +37,22 @@ int sm_count()
 namespace {
 
 enum Phase {
-    kPhBinCount, kPhScanBricks, kPhBinScatter, kPhBrickSort, kPhDenseSelf, kPhDensePairs, kPhLink,
-    kPhFinalize, kPhOutputs, kPhCatalogue, kNumPhases
+    kPhBinCount, kPhScanBricks, kPhBinScatter, kPhBrickSort, kPhTeamSelf, kPhDenseSelf, kPhDensePairs,
+    kPhLink, kPhFinalize, kPhOutputs, kPhCatalogue, kNumPhases
 };
 
 const char* kPhaseNames[kNumPhases] = {
-    "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "dense_self", "dense_pairs", "link",
-    "finalize", "outputs", "catalogue",
+    "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "team_self", "dense_self", "dense_pairs",
+    "link", "finalize", "outputs", "catalogue",
 };
-const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 1, 1, 1, 1, 2, 4};
+const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 1, 1, 1, 1, 1, 2, 4};
 
 constexpr int64_t kMaxTotal = 2147483646LL;   // slots and labels are int32
 constexpr int kDefaultRetryCap = 1 << 20;
 constexpr int kDefaultDenseMin = 256;
 constexpr double kDefaultOccupancy = 0.5;
 constexpr int kDefaultTeamMin = 4;
+constexpr int kMinTeamMin = 2;                 // smallest accepted team threshold (sizes team_list)
 constexpr int kMaxCellsPerAxis = 4096;        // float32 cell-index precision (unsplit cells)
 constexpr int kMaxFinePerAxis = 16384;        // float32 index precision (sub-cells)
 
@@ -186,6 +187,8 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
         b.reach2 = (float)(rf * rf * (1.0 + std::ldexp(1.0, -20)));
     }
     b.team_min = (o && o->reserved[0] > 0) ? o->reserved[0] : kDefaultTeamMin;
+    if (b.team_min < kMinTeamMin)
+        b.team_min = kMinTeamMin;
     // Team bounding-box filter.  A neighbour particle shifted by +-float32(L)
     // and the float32 gaps to the box are each within L 2^-24 (shift: the
     // sum and float32(L); gap: one subtraction) per axis, 3 L 2^-24 together,
@@ -308,7 +311,7 @@ namespace {
 struct Layout {
     size_t boxes, p0, brick0, results, bcount, bstart, bcursor, scan_tmp, tile_cnt, tile_off,
         cell_start, tmp, sorted, parent, minorig, cnt, dense_list, n_dense, dense_root, out_cursor,
-        total;
+        team_list, n_team, total;
     int64_t scan_len, n_tiles, dense_cap;
 };
 
@@ -346,6 +349,8 @@ Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cel
     L.n_dense = take(4);
     L.dense_root = take(4 * (size_t)(total_n / dense_min + 2));
     L.out_cursor = take(4 * (size_t)((total_n >> kOutChunkLog) + 2));
+    L.team_list = take(8 * (size_t)(total_n / kMinTeamMin + 1));
+    L.n_team = take(4);
     L.total = off;
     return L;
 }
@@ -513,6 +518,8 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     w.n_dense = (int*)(ws + L.n_dense);
     w.dense_root = (int*)(ws + L.dense_root);
     w.out_cursor = (int*)(ws + L.out_cursor);
+    w.team_list = (int64_t*)(ws + L.team_list);
+    w.n_team = (int*)(ws + L.n_team);
 
     cudaError_t e = cudaMemcpy(ws + L.boxes, boxes.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -548,9 +555,13 @@ int enqueue_link(fof_plan* h, const float* pos, cudaStream_t s)
     FOF_TRY(launch_bin_scatter(pos, g, w, s));
     phase_end(h, kPhBinScatter, s);
     FOF_TRY(cudaMemsetAsync(w.n_dense, 0, 4, s));
+    FOF_TRY(cudaMemsetAsync(w.n_team, 0, 4, s));
     phase_begin(h, kPhBrickSort, s);
     FOF_TRY(launch_brick_sort(g, w, h->dense_min, s));
     phase_end(h, kPhBrickSort, s);
+    phase_begin(h, kPhTeamSelf, s);
+    FOF_TRY(launch_team_self(g, w, s));
+    phase_end(h, kPhTeamSelf, s);
     phase_begin(h, kPhDenseSelf, s);
     FOF_TRY(launch_dense(g, w, h->dense_min, h->retry_cap, false, s));
     phase_end(h, kPhDenseSelf, s);
@@ -1023,6 +1034,8 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
     w.n_dense = (int*)(ws + L.n_dense);
     w.dense_root = (int*)(ws + L.dense_root);
     w.out_cursor = (int*)(ws + L.out_cursor);
+    w.team_list = (int64_t*)(ws + L.team_list);
+    w.n_team = (int*)(ws + L.n_team);
 
     // The array keeps the previous call's contents: the box table is
     // rewritten and every counter that must start at zero is cleared here.
@@ -1040,7 +1053,9 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
         FOF_TRY(launch_bin_count(pos_dev, g, w, s));
         FOF_TRY(launch_scan(w.bcount, w.bstart, tb, w.scan_tmp, w.scan_tmp_len, s));
         FOF_TRY(launch_bin_scatter(pos_dev, g, w, s));
+        FOF_TRY(cudaMemsetAsync(w.n_team, 0, 4, s));
         FOF_TRY(launch_brick_sort(g, w, kDefaultDenseMin, s));
+        FOF_TRY(launch_team_self(g, w, s));
         FOF_TRY(launch_dense(g, w, kDefaultDenseMin, kDefaultRetryCap, false, s));
         FOF_TRY(launch_dense(g, w, kDefaultDenseMin, kDefaultRetryCap, true, s));
         FOF_TRY(launch_link(g, w, kDefaultDenseMin, kDefaultRetryCap, s));
