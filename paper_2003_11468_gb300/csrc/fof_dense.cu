@@ -116,16 +116,6 @@ __device__ __forceinline__ void lunion(int* lpar, int a, int b, int* err)
     atomicOr(err, kErrInternal);
 }
 
-// half of the 124 offsets in [-2, 2]^3 \ {0}
-__device__ __forceinline__ void half_offset2(int k, int& dx, int& dy, int& dz)
-{
-    // k in [0, 62): code in [63, 125) of (dx+2) + 5 (dy+2) + 25 (dz+2)
-    int code = 63 + k;
-    dx = code % 5 - 2;
-    dy = (code / 5) % 5 - 2;
-    dz = code / 25 - 2;
-}
-
 // Load cell [c0, c0+m) and build its sub-cell structure in shared memory.
 // (ox, oy, oz) = fine coordinates of the cell's corner.  Returns the
 // number of non-empty sub-cells; sets misc[1] on an inconsistency.
