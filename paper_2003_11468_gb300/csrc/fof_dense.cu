@@ -56,7 +56,7 @@ __host__ __device__ constexpr size_t dense_smem_bytes()
            (size_t)kMaxQ3 * 2 + 512 + (size_t)kMaxQ * kMaxQ * 4;
 }
 
-__device__ DenseSmem carve(unsigned char* base)
+__device__ __forceinline__ DenseSmem carve(unsigned char* base)
 {
     DenseSmem s;
     size_t off = 0;
@@ -119,7 +119,7 @@ __device__ __forceinline__ void lunion(int* lpar, int a, int b, int* err)
 // Load cell [c0, c0+m) and build its sub-cell structure in shared memory.
 // (ox, oy, oz) = fine coordinates of the cell's corner.  Returns the
 // number of non-empty sub-cells; sets misc[1] on an inconsistency.
-__device__ int build_cell(const DenseSmem& S, const float4* __restrict__ sorted, int c0, int m,
+__device__ __forceinline__ int build_cell(const DenseSmem& S, const float4* __restrict__ sorted, int c0, int m,
                           const BoxDev& b, int ox, int oy, int oz, int* err)
 {
     const int q = b.q, q3 = q * q * q;
@@ -217,7 +217,7 @@ __device__ __forceinline__ int link_window(const DenseSmem& S, int* parent, cons
                 if (beg == end || S.groot[a] == rj)
                     continue;
                 for (int t = beg; t < end; ++t) {
-                    if (linked(pj, S.P[S.order[t]], b)) {
+                    if (linked_ool(pj, S.P[S.order[t]], b)) {
                         rj = uf_union(parent, rj, S.groot[a], cap, err);
                         linked_any = true;
                         if (single)
@@ -278,7 +278,7 @@ __device__ __forceinline__ int neighbour_of(const DenseSmem& S, int t)
     return lo;
 }
 
-__global__ void __launch_bounds__(kDenseThreads) k_dense_self(Geometry g, Work w, int dense_min,
+__global__ void __launch_bounds__(kDenseThreads, 2) k_dense_self(Geometry g, Work w, int dense_min,
                                                               int cap)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_self(Geometry g, Work w
                     for (int u = a0; u < a1 && !done; ++u) {
                         float4 pu = S.P[S.order[u]];
                         for (int v = b0; v < b1; ++v)
-                            if (linked(pu, S.P[S.order[v]], b)) {
+                            if (linked_ool(pu, S.P[S.order[v]], b)) {
                                 lunion(S.lpar, ra, rb, err);
                                 done = true;
                                 break;
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_self(Geometry g, Work w
     }
 }
 
-__global__ void __launch_bounds__(kDenseThreads) k_dense_pairs(Geometry g, Work w, int dense_min,
+__global__ void __launch_bounds__(kDenseThreads, 2) k_dense_pairs(Geometry g, Work w, int dense_min,
                                                                int cap)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -210,6 +210,18 @@ __device__ __forceinline__ bool linked(const float4& p, const float4& q, const B
         return false;
     if (s < b.t_lo)
         return true;
+    return linked_exact_inl(p, q, b.L, b.l2);
+}
+
+// The same predicate with the band test out of line: fewer registers where
+// the caller keeps much state live (the dense cell kernels).
+__device__ __forceinline__ bool linked_ool(const float4& p, const float4& q, const BoxDev& b)
+{
+    float s = d2_f32(p, q, b.Lf);
+    if (s > b.t_hi)
+        return false;
+    if (s < b.t_lo)
+        return true;
     return linked_exact(p, q, b.L, b.l2);
 }
 
