@@ -82,7 +82,7 @@ typedef struct {
 typedef struct {
     int32_t cells_per_axis;  /* cells per box side; must keep side >= l_x   */
     int32_t brick_cells;     /* cells per brick side: 1, 2, 4, 8 or 16      */
-    double occupancy;        /* target mean particles per cell (default 0.5) */
+    double occupancy;        /* target mean particles per cell (default 0.35) */
     int32_t dense_min;       /* cell occupancy from which a cell is split
                                 into sub-cells and linked in shared memory
                                 (default 256)                                */
@@ -247,7 +247,7 @@ const char *fof_strerror(int code);
  * which every GPU that loads the library holds until the process exits.
  *   - Problems whose workspace (fof_workspace_bytes with NULL options)
  *     exceeds 32 MiB are rejected with FOF_ERR_TOO_LARGE, checked before any
- *     pointer; that is about 600,000 particles at the default occupancy.
+ *     pointer; that is about 580,000 particles at the default occupancy.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

@@ -22,7 +22,7 @@ CASES = [
     (3.0, 0.0371, 5000),
     (77.7, 0.9, 100000),
     (12.5, 0.2 * 100 / 1024, 128 ** 3),
-    (1.0, 0.3, 1000),            # few cells: sub-cells are off
+    (1.0, 0.3, 1000),            # 3 cells per axis
 ]
 
 
@@ -82,6 +82,11 @@ def test_linked_pairs_stay_in_the_stencil(case):
 def test_fine_cells_are_cliques(case):
     box, l_x, n = CASES[case]
     gm = fof.fof_box_geometry(box, l_x, n)
+    if gm.sub_cells == 1:
+        # larger cells at a higher occupancy are split
+        opt = fof.fof_options()
+        opt.occupancy = 4.0
+        gm = fof.fof_box_geometry(box, l_x, n, opt)
     if gm.sub_cells == 1:
         pytest.skip("cells are not split for this box")
     rng = np.random.default_rng(100 + case)
