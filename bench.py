@@ -51,6 +51,9 @@ def workloads():
     from paper_2003_11468_gb300 import synth
     return {
         "1024": synth.clustered_1024,
+        # 1/64 of the 1024^3 box at the same density, blob recipe and l_x:
+        # the small case the per-kernel ncu captures run on
+        "1024s": lambda: synth.clustered_sample_of_1024(4),
         "256": synth.clustered_256,
         "32k": synth.uniform_32k,
     }
@@ -509,7 +512,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="1024", choices=["1024", "256", "32k", "batch", "served"])
+    ap.add_argument("--workload", default="1024", choices=["1024", "1024s", "256", "32k", "batch", "served"])
     ap.add_argument("--boxes", type=int, default=512, help="batch workload: number of boxes")
     ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
     ap.add_argument("--pool", type=int, default=24, help="served workload: distinct inputs")
