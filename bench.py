@@ -387,8 +387,18 @@ def run_batch(args):
     concat = torch.from_numpy(np.concatenate(poss)).cuda()
     offs = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
     stream = torch.cuda.Stream()
+    boxes, lxs = [sp["box"] for sp in specs], [sp["l_x"] for sp in specs]
+    # plan options picked by the autotuner on this batch (untimed; FOF_TUNE_CACHE caches them)
+    opt, tuned, t_tune = None, None, 0.0
+    if not args.no_tune:
+        from paper_2003_11468_gb300 import tune
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            opt, rep = tune.tune(boxes, lxs, ns, concat, repeats=1, min_size=20, stream=stream)
+        t_tune = time.perf_counter() - t0
+        tuned = {"options": rep["best"], "key": rep["key"], "cached": rep["cached"]}
     # batched: one plan, one graph
-    h = fof.fof_batch_create([sp["box"] for sp in specs], [sp["l_x"] for sp in specs], ns)
+    h = fof.fof_batch_create(boxes, lxs, ns, opt)
     ids_b = torch.empty(total, dtype=torch.int32, device="cuda")
     sizes_b = torch.empty_like(ids_b)
     cat_b = torch.empty((total, 2), dtype=torch.int32, device="cuda")
@@ -406,7 +416,7 @@ def run_batch(args):
     code, ng, nk = fof.fof_result(h, len(specs), stream)
     ms_batch = e0.elapsed_time(e1) / args.steps
     # plain loop: a plan per box (created beforehand), link + groups per box
-    plans = [fof.fof_create(sp["box"], sp["l_x"], sp["n"]) for sp in specs]
+    plans = [fof.fof_create_ex(sp["box"], sp["l_x"], sp["n"], opt) for sp in specs]
     ids_p = torch.empty(total, dtype=torch.int32, device="cuda")
     sizes_p = torch.empty_like(ids_p)
     cat_p = torch.empty((total, 2), dtype=torch.int32, device="cuda")
@@ -434,7 +444,7 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": f"batch of {len(specs)} clustered boxes", "particles": total,
-                       "status": code},
+                       "status": code, "tuned": tuned, "tune_s": t_tune},
             "plain_loop": {"value": total / (ms_plain * 1e-3), "unit": UNIT, "ms_per_step": ms_plain},
             "speedup_vs_plain": ms_plain / ms_batch, "identical_to_plain": exact,
             "gpu_launches": None, "clocks": clk, "gen_s": t_gen}
@@ -512,11 +522,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: library default options")
     ap.add_argument("--workload", default="1024", choices=["1024", "1024s", "256", "32k", "batch", "served"])
     ap.add_argument("--boxes", type=int, default=512, help="batch workload: number of boxes")
     ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
     ap.add_argument("--pool", type=int, default=24, help="served workload: distinct inputs")
-    ap.add_argument("--slots", type=int, default=2)
+    ap.add_argument("--slots", type=int, default=3)
     ap.add_argument("--budget-gb", type=int, default=120)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -14,8 +14,11 @@ of very different sizes arriving at random times.  This server
 * runs each batch on its slot's stream (H2D copy, `fof_link`,
   `fof_groups_async`, D2H copy of ids, sizes and the catalogue), so batches
   on different slots overlap on the device;
-* polls completion events, reads the status (`fof_result`), resolves the
-  futures, returns the batch's share of the budget and admits more work.
+* polls completion events and hands finished batches to a completion
+  thread, which reads the status (`fof_result`), copies each request's
+  results out of the slot's pinned buffers with a pool of host threads,
+  resolves the futures and only then returns the slot and the batch's share
+  of the budget; the scheduler meanwhile keeps admitting and launching.
 
 Results are exactly those of a solo run (the partition is unique).  Memory
 comes from PyTorch's caching allocator, the only allocator used.
@@ -23,9 +26,10 @@ comes from PyTorch's caching allocator, the only allocator used.
 from __future__ import annotations
 
 import collections
+import os
 import threading
 import time
-from concurrent.futures import Future
+from concurrent.futures import Future, ThreadPoolExecutor, wait
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -125,21 +129,35 @@ class _Batch:
             b.sizes_h[:t].copy_(b.sizes[:t], non_blocking=True)
             self.event.record(self.stream)
 
-    def finish(self):
+    # elements per host copy task: large enough to amortise the task, small
+    # enough to spread one big request over the copy threads
+    COPY_CHUNK = 1 << 22
+
+    def finish(self, copy_pool):
         code, ng, nk = fof.fof_result(self.h, len(self.reqs), self.stream)
         b = self.b
         ids = b.ids_h.numpy()
         sizes = b.sizes_h.numpy()
         cat = b.cat[: int(sum(nk))].cpu().numpy()     # only the rows that exist
+        outs = [(np.empty(n, np.int32), np.empty(n, np.int32)) for n in self.ns]
+
+        def copy(i, a, e):
+            o = int(self.offsets[i])
+            outs[i][0][a:e] = ids[o + a:o + e]
+            outs[i][1][a:e] = sizes[o + a:o + e]
+
+        tasks = [copy_pool.submit(copy, i, a, min(a + self.COPY_CHUNK, n))
+                 for i, n in enumerate(self.ns) for a in range(0, n, self.COPY_CHUNK)]
+        wait(tasks)
+        for t in tasks:
+            t.result()
         now = time.perf_counter()
         k0 = 0
         for i, r in enumerate(self.reqs):
-            o0, o1 = self.offsets[i], self.offsets[i + 1]
             rows = cat[k0:k0 + nk[i]]
             k0 += nk[i]
             rows = rows[rows[:, 1] >= max(r.min_size, 1)].copy()
-            r.future.set_result(Result(ids[o0:o1].copy(), sizes[o0:o1].copy(), rows, ng[i],
-                                       now - r.t_arrive))
+            r.future.set_result(Result(outs[i][0], outs[i][1], rows, ng[i], now - r.t_arrive))
         fof.fof_destroy(self.h)
         self.h = None
 
@@ -152,10 +170,12 @@ class Server:
     max_batch_boxes / max_batch_particles: limits of one batch plan.
     prealloc: optional (box, l_x, n) of the largest batch expected; every
     slot's buffers are sized for it up front.
+    copy_threads: host threads that copy results out of the slot buffers.
     """
 
-    def __init__(self, memory_budget: int = 120 << 30, slots: int = 2, max_batch_boxes: int = 64,
-                 max_batch_particles: int = 1 << 27, device: int = 0, prealloc=None):
+    def __init__(self, memory_budget: int = 120 << 30, slots: int = 3, max_batch_boxes: int = 64,
+                 max_batch_particles: int = 1 << 27, device: int = 0, prealloc=None,
+                 copy_threads: int | None = None):
         import torch
         fof.load()
         self.device = torch.device("cuda", device)
@@ -174,6 +194,11 @@ class Server:
         self.free_slots = list(range(slots))
         self.waiting = collections.deque()
         self.running = []
+        self.finishing = 0
+        nthr = copy_threads or max(1, min(8, (os.cpu_count() or 2) // 2))
+        self.copy_pool = ThreadPoolExecutor(max_workers=nthr)
+        self.completer = ThreadPoolExecutor(max_workers=1, initializer=torch.cuda.set_device,
+                                            initargs=(self.device,))
         self.lock = threading.Condition()
         self.stop_flag = False
         self.latencies = []
@@ -194,6 +219,8 @@ class Server:
             self.stop_flag = True
             self.lock.notify()
         self.thread.join()
+        self.completer.shutdown(wait=True)
+        self.copy_pool.shutdown(wait=True)
 
     def __enter__(self):
         return self
@@ -223,7 +250,7 @@ class Server:
             need += b
             total += n
         if not take:
-            if not self.running and self.waiting:
+            if not self.running and not self.finishing and self.waiting:
                 # a single request larger than the budget can never run
                 req = self.waiting.popleft()
                 req.future.set_exception(MemoryError("request exceeds the memory budget"))
@@ -243,30 +270,44 @@ class Server:
         batch.launch()
         return batch
 
+    def _complete(self, b):
+        """Completion thread: results out, futures resolved, slot returned."""
+        try:
+            b.finish(self.copy_pool)
+        except Exception as e:                      # a failed batch fails its requests
+            for r in b.reqs:
+                if not r.future.done():
+                    r.future.set_exception(e)
+        with self.lock:
+            self.in_use -= b.reserved
+            self.free_slots.append(b.slot)
+            self.finishing -= 1
+            for r in b.reqs:
+                if r.future.exception() is None:
+                    self.latencies.append(r.future.result().latency_s)
+            self.completed_particles += b.total
+            self.lock.notify()
+
     def _loop(self):
         import torch
         torch.cuda.set_device(self.device)
         while True:
             with self.lock:
-                if self.stop_flag and not self.waiting and not self.running:
+                if self.stop_flag and not self.waiting and not self.running and not self.finishing:
                     return
                 while True:
                     b = self._admit()
                     if b is None:
                         break
                     self.running.append(b)
-                if not self.running and not self.waiting:
+                if not self.running and (not self.waiting or self.finishing):
                     self.lock.wait(timeout=0.05)
                     continue
             done = [b for b in self.running if b.event.query()]
             for b in done:
-                b.finish()
                 with self.lock:
                     self.running.remove(b)
-                    self.in_use -= b.reserved
-                    self.free_slots.append(b.slot)
-                    for r in b.reqs:
-                        self.latencies.append(r.future.result().latency_s)
-                    self.completed_particles += b.total
+                    self.finishing += 1
+                self.completer.submit(self._complete, b)
             if not done:
                 time.sleep(0.0002)
