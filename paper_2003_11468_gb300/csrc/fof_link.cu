@@ -389,7 +389,10 @@ constexpr float kFar = 1e30f;
 // Tests of lane i's particle against particles jb*32 + t, t < jn8 (a
 // multiple of 8), returning row i's word of block jb.  For an off-diagonal
 // block (kOff) the ballot of each test is row j's word of block ib and is
-// stored by lane 0.  Inside one cell no pair needs the periodic wrap when
+// stored by lane 0.  The float32 pre-test decides a group of 8 pairs in an
+// unrolled loop; pairs in the uncertainty band take the exact test after the
+// group, in a loop entered only when some lane has one, so the unrolled body
+// stays small.  Inside one cell no pair needs the periodic wrap when
 // the box has at least 3 cells per axis (the cell side is then below L/2,
 // so the wrapped float32 separation equals the plain difference); kWrap
 // takes the full predicate for boxes with fewer cells.
@@ -401,30 +404,39 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem& S, i
     unsigned* colp = &S.adj[jb * 32 * kAdjStride + ib];
     unsigned row = 0;
     for (int t0 = 0; t0 < jn8; t0 += 8) {
-        unsigned byte = 0;
+        // 8 pre-tests: certainly linked (below t_lo) or undecided (the band)
+        unsigned byte = 0, band = 0;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const float4 q = pj[t0 + u];
-            bool lk;
+            float s2;
             if (kWrap) {
-                const float s2 = d2_f32(pi, q, b.Lf);
-                lk = s2 <= b.t_hi;
-                if (lk && !(s2 < b.t_lo))
-                    lk = linked_exact_inl(pi, q, b.L, b.l2);
+                s2 = d2_f32(pi, q, b.Lf);
             } else {
                 const float dx = __fsub_rn(pi.x, q.x);
                 const float dy = __fsub_rn(pi.y, q.y);
                 const float dz = __fsub_rn(pi.z, q.z);
-                const float s2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                lk = s2 <= b.t_hi;
-                if (lk && !(s2 < b.t_lo))
-                    lk = linked_exact_inl(pi, q, b.L, b.l2);
+                s2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
             }
+            const bool lk = s2 < b.t_lo;
             byte |= (unsigned)lk << u;
+            band |= (unsigned)(!lk && s2 <= b.t_hi) << u;
             if (kOff) {
                 const unsigned c = __ballot_sync(kFull, lk);
                 if (lane == 0)
                     colp[(t0 + u) * kAdjStride] = c;
+            }
+        }
+        // the exact test for the undecided pairs (rare)
+        if (__any_sync(kFull, band != 0u)) {
+            for (int u = 0; u < 8; ++u) {
+                const bool ex = ((band >> u) & 1u) && linked_exact_inl(pi, pj[t0 + u], b.L, b.l2);
+                byte |= (unsigned)ex << u;
+                if (kOff) {
+                    const unsigned c = __ballot_sync(kFull, ex);
+                    if (c && lane == 0)
+                        colp[(t0 + u) * kAdjStride] |= c;
+                }
             }
         }
         row |= byte << t0;
@@ -483,7 +495,8 @@ __global__ void __launch_bounds__(kTeamWarps * 32, 4) k_team_self(Geometry g, co
         }
         const BoxDev& b = g.boxes[box_of(g.box_p0, g.nbox, c0)];
 
-        // adjacency rows
+        // adjacency rows (row1: the only word when nw == 1)
+        unsigned row1 = 0u;
         for (int ib = 0; ib < nw; ++ib) {
             const int i = ib * 32 + lane;
             const float4 pi = i < m ? S.P[i] : make_float4(-kFar, -kFar, -kFar, 0.f);
@@ -499,9 +512,33 @@ __global__ void __launch_bounds__(kTeamWarps * 32, 4) k_team_self(Geometry g, co
                 }
                 if (jb == ib)
                     row &= ~(1u << lane);      // the particle itself
-                if (i < m)
+                if (nw == 1)
+                    row1 = i < m ? row : 0u;
+                else if (i < m)
                     S.adj[i * kAdjStride + jb] = row;
             }
+        }
+        if (nw == 1) {
+            // up to 32 particles: lane i keeps row i in a register, and a BFS
+            // step is one OR-reduction of the frontier's rows
+            unsigned todo = __ballot_sync(kFull, row1 != 0u);
+            while (todo) {
+                const int s = __ffs(todo) - 1;
+                unsigned comp = 1u << s, front = comp;
+                for (int step = 0; step < 32; ++step) {   // every step adds a vertex
+                    const unsigned nxt =
+                        __reduce_or_sync(kFull, ((front >> lane) & 1u) ? row1 : 0u) & ~comp;
+                    if (!nxt)
+                        break;
+                    comp |= nxt;
+                    front = nxt;
+                }
+                todo &= ~comp;
+                if (((comp >> lane) & 1u) && lane != s)
+                    parent[c0 + lane] = c0 + s;
+            }
+            __syncwarp();                      // smem reused by the next cell
+            continue;
         }
         __syncwarp();
 
