@@ -366,19 +366,29 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
 // order of their smallest member s, and every member's parent is set to s.
 // Isolated particles keep parent = self.  The kernel runs before any kernel
 // that links across cells, so no other thread touches these parents.
+// The kernel is instantiated for cells of up to 128 particles (half the
+// shared memory and registers, twice the resident warps) and for 129..256.
 constexpr int kTeamWarps = 4;
-constexpr int kTeamMax = kTeamSelfMax;
-constexpr int kTeamWords = kTeamMax / 32;
-constexpr int kAdjStride = kTeamWords + 1;          // odd stride: conflict-free rows
 
+template <int kMax>
 struct TeamSmem {
-    float4 P[kTeamMax];
-    unsigned adj[kTeamMax * kAdjStride];
+    static constexpr int kWords = kMax / 32;
+    static constexpr int kStride = kWords + 1;         // odd stride: conflict-free rows
+    float4 P[kMax];
+    unsigned adj[kMax * kStride];
 };
 
+// resident blocks per SM the instantiation is compiled for (registers)
+template <int kMax>
+constexpr int team_blocks()
+{
+    return kMax <= 128 ? 5 : 4;
+}
+
+template <int kMax>
 size_t team_smem_bytes()
 {
-    return sizeof(TeamSmem) * kTeamWarps;
+    return sizeof(TeamSmem<kMax>) * kTeamWarps;
 }
 
 // Positions that link to nothing: rows and columns beyond the cell's
@@ -396,10 +406,11 @@ constexpr float kFar = 1e30f;
 // the box has at least 3 cells per axis (the cell side is then below L/2,
 // so the wrapped float32 separation equals the plain difference); kWrap
 // takes the full predicate for boxes with fewer cells.
-template <bool kOff, bool kWrap>
-__device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem& S, int jb, int ib, int jn8,
+template <int kMax, bool kOff, bool kWrap>
+__device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>& S, int jb, int ib, int jn8,
                                                 int lane, const BoxDev& b)
 {
+    constexpr int kAdjStride = TeamSmem<kMax>::kStride;
     const float4* pj = &S.P[jb * 32];
     unsigned* colp = &S.adj[jb * 32 * kAdjStride + ib];
     unsigned row = 0;
@@ -446,24 +457,30 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem& S, i
 
 // Positions of a listed cell (size << 32 | first slot) into registers:
 // lane k holds particles k, k + 32, ...
-__device__ __forceinline__ void team_fetch(float4 (&R)[kTeamWords], int64_t e, const float4* __restrict__ sorted,
+template <int kMin, int kMax>
+__device__ __forceinline__ void team_fetch(float4 (&R)[kMax / 32], int64_t e, const float4* __restrict__ sorted,
                                            int lane)
 {
-    const int c0 = (int)(uint32_t)e, m = min((int)(e >> 32), kTeamMax);
+    const int c0 = (int)(uint32_t)e, m = (int)(e >> 32);
+    if (m <= kMin || m > kMax)                 // another instantiation's cell
+        return;
 #pragma unroll
-    for (int r = 0; r < kTeamWords; ++r)
+    for (int r = 0; r < kMax / 32; ++r)
         if (lane + 32 * r < m)
             R[r] = sorted[c0 + lane + 32 * r];
 }
 
-__global__ void __launch_bounds__(kTeamWarps * 32, 4) k_team_self(Geometry g, const int64_t* __restrict__ list,
-                                                              const int* __restrict__ n_list,
-                                                              const float4* __restrict__ sorted,
-                                                              int* __restrict__ parent, int* err)
+template <int kMin, int kMax>
+__global__ void __launch_bounds__(kTeamWarps * 32, team_blocks<kMax>())
+    k_team_self(Geometry g, const int64_t* __restrict__ list, const int* __restrict__ n_list,
+                const float4* __restrict__ sorted, int* __restrict__ parent, int* err)
 {
+    constexpr int kTeamMax = kMax;
+    constexpr int kTeamWords = kMax / 32;
+    constexpr int kAdjStride = TeamSmem<kMax>::kStride;
     extern __shared__ float4 team_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    TeamSmem& S = reinterpret_cast<TeamSmem*>(team_raw)[wid];
+    TeamSmem<kMax>& S = reinterpret_cast<TeamSmem<kMax>*>(team_raw)[wid];
     const int n = *n_list;
     const int stride = gridDim.x * kTeamWarps;
     // software pipeline: the next cell's positions are loaded into
@@ -471,12 +488,13 @@ __global__ void __launch_bounds__(kTeamWarps * 32, 4) k_team_self(Geometry g, co
     int it = blockIdx.x * kTeamWarps + wid;
     int64_t e = it < n ? list[it] : 0;
     float4 R[kTeamWords];
-    team_fetch(R, e, sorted, lane);
+    team_fetch<kMin, kMax>(R, e, sorted, lane);
     int64_t e_next = it + stride < n ? list[it + stride] : 0;
     for (; it < n; it += stride) {
         const int c0 = (int)(uint32_t)e, m = (int)(e >> 32);
         const int nw = (m + 31) >> 5;
-        if (m <= kTeamMax) {
+        const bool in_range = m > kMin && m <= kMax;
+        if (in_range) {
 #pragma unroll
             for (int r = 0; r < kTeamWords; ++r) {   // the ragged tail links nothing
                 const int k = lane + 32 * r;
@@ -487,12 +505,10 @@ __global__ void __launch_bounds__(kTeamWarps * 32, 4) k_team_self(Geometry g, co
         __syncwarp();
         e = e_next;
         if (it + stride < n)
-            team_fetch(R, e, sorted, lane);
+            team_fetch<kMin, kMax>(R, e, sorted, lane);
         e_next = it + 2 * stride < n ? list[it + 2 * stride] : 0;
-        if (m > kTeamMax) {                    // not a team cell: the list is inconsistent
-            if (lane == 0) atomicOr(err, kErrInternal);
+        if (!in_range)                         // another instantiation's cell
             continue;
-        }
         const BoxDev& b = g.boxes[box_of(g.box_p0, g.nbox, c0)];
 
         // adjacency rows (row1: the only word when nw == 1)
@@ -504,11 +520,11 @@ __global__ void __launch_bounds__(kTeamWarps * 32, 4) k_team_self(Geometry g, co
                 const int jn8 = (min(32, m - jb * 32) + 7) & ~7;
                 unsigned row;
                 if (b.nc >= 3) {
-                    row = jb == ib ? block_tests<false, false>(pi, S, jb, ib, jn8, lane, b)
-                                   : block_tests<true, false>(pi, S, jb, ib, jn8, lane, b);
+                    row = jb == ib ? block_tests<kMax, false, false>(pi, S, jb, ib, jn8, lane, b)
+                                   : block_tests<kMax, true, false>(pi, S, jb, ib, jn8, lane, b);
                 } else {
-                    row = jb == ib ? block_tests<false, true>(pi, S, jb, ib, jn8, lane, b)
-                                   : block_tests<true, true>(pi, S, jb, ib, jn8, lane, b);
+                    row = jb == ib ? block_tests<kMax, false, true>(pi, S, jb, ib, jn8, lane, b)
+                                   : block_tests<kMax, true, true>(pi, S, jb, ib, jn8, lane, b);
                 }
                 if (jb == ib)
                     row &= ~(1u << lane);      // the particle itself
@@ -611,12 +627,19 @@ cudaError_t launch_team_self(const Geometry& g, const Work& w, cudaStream_t s)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(k_team_self, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)team_smem_bytes());
+        e = cudaFuncSetAttribute(k_team_self<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)team_smem_bytes<128>());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_team_self<128, kTeamSelfMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)team_smem_bytes<kTeamSelfMax>());
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    k_team_self<<<sm_count() * 4, kTeamWarps * 32, team_smem_bytes(), s>>>(
+    k_team_self<0, 128><<<sm_count() * team_blocks<128>(), kTeamWarps * 32, team_smem_bytes<128>(), s>>>(
+        g, w.team_list, w.n_team, w.sorted, w.parent, &w.status->err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_team_self<128, kTeamSelfMax><<<sm_count() * team_blocks<kTeamSelfMax>(), kTeamWarps * 32, team_smem_bytes<kTeamSelfMax>(), s>>>(
         g, w.team_list, w.n_team, w.sorted, w.parent, &w.status->err);
     return cudaGetLastError();
 }
