@@ -159,6 +159,27 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Every rank groups its own independent box of the same recipe."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (all ranks get it); no-op for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the particles all ranks grouped / the slowest rank's time."""
+    return world * n_per_rank / seconds
+
+
 # ---------------------------------------------------------------------------
 # the CPU oracle arm (and the cpu_baseline key)
 # ---------------------------------------------------------------------------
@@ -234,7 +255,7 @@ def run_gpu(args):
     wl = workloads()[args.workload]()
     t_gen = time.perf_counter()
     # every rank its own independent box of the same recipe
-    pos_np = wl["make"](seed=wl["seed"] + 1000 * rank)
+    pos_np = wl["make"](seed=rank_seed(wl["seed"], rank))
     t_gen = time.perf_counter() - t_gen
     n, box, l_x, min_size = wl["n"], wl["box"], wl["l_x"], wl["min_size"]
 
@@ -276,11 +297,8 @@ def run_gpu(args):
         res = step()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
-    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
         torch.distributed.barrier()
     clocks = sampler.stop()
     launches = fof.fof_kernel_launches(h) - launches0
@@ -288,7 +306,7 @@ def run_gpu(args):
     fof.fof_set_timing(h, False)
     code, ng, nk = res
     ms_step = ms_total / args.steps
-    value = world * n / (ms_step * 1e-3)
+    value = job_value(n, world, ms_step * 1e-3)
 
     # dominant kernel and its roofline
     peak, peak_kind = peaks()
@@ -316,12 +334,8 @@ def run_gpu(args):
         for _ in range(args.steps):
             _, _, nk_h = fof.fof_run_host(h, pos_pin, ids_h, sizes_h, cat_h, cap, min_size, 1, stream)
         torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * n * args.steps / dt, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_value(n * args.steps, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": 12 * n,
                "d2h_bytes_per_step": 8 * n + 8 * min(nk_h[0], cap) + 64 + 16}
 
