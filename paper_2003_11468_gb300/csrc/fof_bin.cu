@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
 {
     __shared__ int hist[kMaxR3];
     __shared__ int sw[32];
+    __shared__ int list_base[2];
     for (int64_t gb = blockIdx.x; gb < g.total_bricks; gb += gridDim.x) {
         const int bi = box_of(g.box_brick0, g.nbox, gb);
         const BoxDev& b = g.boxes[bi];
@@ -232,17 +233,40 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
         for (int c = c0; c < c0 + per && c < r3; ++c) run += hist[c];
         int total;
         int ex = block_exclusive_scan(run, sw, total);
+        const int ex0 = ex;
         const int64_t cbase = b.cell0 + (gb - b.brick0) * (int64_t)r3;
+        int nd = 0, nt = 0;                     // this thread's dense and team cells
+        for (int c = c0; c < c0 + per && c < r3; ++c) {
+            const int h = hist[c];
+            cell_start[cbase + c] = s0 + ex;
+            ex += h;
+            if (is_sub(h, b, dense_min))
+                ++nd;
+            else if (h >= b.team_min && h <= kTeamSelfMax)
+                ++nt;
+        }
+        // list slots: one reservation per brick (a shared counter per cell
+        // would serialise millions of atomics on one address)
+        int nd_tot, nt_tot;
+        int od = block_exclusive_scan(nd, sw, nd_tot);
+        int ot = block_exclusive_scan(nt, sw, nt_tot);
+        if (threadIdx.x == 0) {
+            list_base[0] = nd_tot ? atomicAdd(n_dense, nd_tot) : 0;
+            list_base[1] = nt_tot ? atomicAdd(n_team, nt_tot) : 0;
+        }
+        __syncthreads();
+        od += list_base[0];
+        ot += list_base[1];
+        ex = ex0;
         for (int c = c0; c < c0 + per && c < r3; ++c) {
             const int h = hist[c];
             const int start = s0 + ex;
             hist[c] = ex;                       // becomes the cursor
-            cell_start[cbase + c] = start;
             ex += h;
             if (is_sub(h, b, dense_min))
-                dense_list[atomicAdd(n_dense, 1)] = cbase + c;
+                dense_list[od++] = cbase + c;
             else if (h >= b.team_min && h <= kTeamSelfMax)
-                team_list[atomicAdd(n_team, 1)] = ((int64_t)h << 32) | (uint32_t)start;
+                team_list[ot++] = ((int64_t)h << 32) | (uint32_t)start;
         }
         __syncthreads();
         for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {

@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(256) k_outputs_bucket(Geometry g, const float4
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int acc_box = -1;                           // per-warp box counts not yet added
+    unsigned long long acc_ng = 0, acc_nk = 0;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.total_n; base += stride) {
         int64_t s = base + threadIdx.x;
         bool valid = s < g.total_n;
@@ -114,17 +116,39 @@ __global__ void __launch_bounds__(256) k_outputs_bucket(Geometry g, const float4
         }
         bool is_root = root == (int)s;
         bool in_cat = is_root && size >= thr;
-        // per-box counts, aggregated over lanes of the same box
-        unsigned bpeers = __match_any_sync(active, bi);
-        int bleader = __ffs(bpeers) - 1;
-        int ng = __popc(__ballot_sync(active, is_root) & bpeers);
-        int nk = __popc(__ballot_sync(active, in_cat) & bpeers);
-        if (lane == bleader) {
-            if (ng) atomicAdd(n_groups + bi, (unsigned long long)ng);
-            if (nk) atomicAdd(n_cat + bi, (unsigned long long)nk);
+        // per-box counts: summed in registers while the warp stays inside one
+        // box and added once per box (one counter per box would otherwise
+        // take an atomic from every warp, all on one address)
+        const int bi0 = __shfl_sync(active, bi, 0);
+        const unsigned roots = __ballot_sync(active, is_root), cats = __ballot_sync(active, in_cat);
+        if (__all_sync(active, bi == bi0)) {
+            if (bi0 != acc_box) {
+                if (lane == 0 && acc_box >= 0) {
+                    if (acc_ng) atomicAdd(n_groups + acc_box, acc_ng);
+                    if (acc_nk) atomicAdd(n_cat + acc_box, acc_nk);
+                }
+                acc_box = bi0;
+                acc_ng = acc_nk = 0;
+            }
+            acc_ng += __popc(roots);
+            acc_nk += __popc(cats);
+        } else {
+            unsigned bpeers = __match_any_sync(active, bi);
+            int bleader = __ffs(bpeers) - 1;
+            int ng = __popc(roots & bpeers);
+            int nk = __popc(cats & bpeers);
+            if (lane == bleader) {
+                if (ng) atomicAdd(n_groups + bi, (unsigned long long)ng);
+                if (nk) atomicAdd(n_cat + bi, (unsigned long long)nk);
+            }
         }
         if (in_cat)
             atomicAdd(tile_cnt + (p0 + label) / kCatTile, 1);
+    }
+    // lane 0 took part in every iteration (its slot is the warp's smallest)
+    if (lane == 0 && acc_box >= 0) {
+        if (acc_ng) atomicAdd(n_groups + acc_box, acc_ng);
+        if (acc_nk) atomicAdd(n_cat + acc_box, acc_nk);
     }
 }
 
