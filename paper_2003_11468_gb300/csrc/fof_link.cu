@@ -80,6 +80,12 @@ __device__ __forceinline__ unsigned reach_mask(const float4& p, const BoxDev& b,
     return (hz ? m9 : 0u) | (hy ? xm << 9 : 0u) | (hx << 12);
 }
 
+// Team cells from this size on (more than one warp word) are stored in z
+// order (k_team_self) and their z-prefix searched by the streams of the
+// cells below them (k_link); sorting the many small cells costs more than it
+// saves.
+constexpr int kSortMin = 33;
+
 __device__ __forceinline__ float4 shfl4(float4 v, int src)
 {
     v.x = __shfl_sync(kFull, v.x, src);
@@ -329,6 +335,24 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
                     cntk = j1 - j0;
                 }
             }
+            // Neighbours k < 9 lie one cell up in z.  A team cell there (sorted
+            // by z in k_team_self) is cut to the prefix that the box filter can
+            // pass: past it, the z gap to the team alone squares above
+            // bb_reach2 (the filter's sum only adds non-negative terms, and
+            // the gap only grows along the z order).
+            if (lane < 9 && b.nc >= 3 && cntk >= kSortMin && cntk >= b.team_min && cntk <= kTeamSelfMax) {
+                const float sz = tc.cz + 1 >= b.nc ? b.Lf : 0.f;
+                int lo = 0, hi = cntk;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const float d = __fsub_rn(__fadd_rn(sorted[j0k + mid].z, sz), tbx.hz);
+                    if (d > 0.f && __fmul_rn(d, d) > b.bb_reach2)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                cntk = lo;
+            }
             team_stream(parent, sorted, b, mine, reach, p, ri, last, tc, j0k, cntk, tbx, b.nc >= 3, cap,
                         err);
         }
@@ -382,7 +406,7 @@ struct TeamSmem {
 template <int kMax>
 constexpr int team_blocks()
 {
-    return kMax <= 128 ? 5 : 4;
+    return 4;
 }
 
 template <int kMax>
@@ -458,8 +482,7 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
 // Positions of a listed cell (size << 32 | first slot) into registers:
 // lane k holds particles k, k + 32, ...
 template <int kMin, int kMax>
-__device__ __forceinline__ void team_fetch(float4 (&R)[kMax / 32], int64_t e, const float4* __restrict__ sorted,
-                                           int lane)
+__device__ __forceinline__ void team_fetch(float4 (&R)[kMax / 32], int64_t e, const float4* sorted, int lane)
 {
     const int c0 = (int)(uint32_t)e, m = (int)(e >> 32);
     if (m <= kMin || m > kMax)                 // another instantiation's cell
@@ -470,10 +493,71 @@ __device__ __forceinline__ void team_fetch(float4 (&R)[kMax / 32], int64_t e, co
             R[r] = sorted[c0 + lane + 32 * r];
 }
 
+// Sorts the staged cell (nw * 32 entries of S.P, sentinels after the cell's
+// particles) by z, exact float order: a bitonic network over 32-bit keys
+// (z >= 0, so the float bits order like the values) and their indices in the
+// adjacency area, which is free until the adjacency is built, then the
+// entries are permuted into place.
+template <int kMax>
+__device__ __forceinline__ void sort_cell_z(TeamSmem<kMax>& S, int nw, int lane)
+{
+    const int n = nw * 32;
+    int n2 = 32;
+    while (n2 < n) n2 <<= 1;                   // <= kMax
+    unsigned* key = S.adj;
+    unsigned short* id = reinterpret_cast<unsigned short*>(S.adj + kMax);
+    for (int k = lane; k < n2; k += 32) {
+        key[k] = k < n ? __float_as_uint(S.P[k].z) : 0xFFFFFFFFu;
+        id[k] = (unsigned short)k;
+    }
+    __syncwarp();
+    for (int size = 2; size <= n2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < n2; i += 32) {
+                const int l = i ^ stride;
+                if (l > i) {
+                    const unsigned ki = key[i], kl = key[l];
+                    if ((ki > kl) == ((i & size) == 0)) {
+                        key[i] = kl;
+                        key[l] = ki;
+                        const unsigned short t = id[i];
+                        id[i] = id[l];
+                        id[l] = t;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if constexpr (kMax <= 128) {
+        // through registers: every read before any write
+        float4 v[kMax / 32];
+#pragma unroll
+        for (int r = 0; r < kMax / 32; ++r)
+            if (lane + 32 * r < n)
+                v[r] = S.P[id[lane + 32 * r]];
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kMax / 32; ++r)
+            if (lane + 32 * r < n)
+                S.P[lane + 32 * r] = v[r];
+    } else {
+        // through a copy in the rest of the adjacency area
+        static_assert(kMax + kMax / 2 + 4 * kMax <= kMax * TeamSmem<kMax>::kStride, "scratch");
+        float4* copy = reinterpret_cast<float4*>(S.adj + kMax + kMax / 2);
+        for (int k = lane; k < n; k += 32)
+            copy[k] = S.P[k];
+        __syncwarp();
+        for (int k = lane; k < n; k += 32)
+            S.P[k] = copy[id[k]];
+    }
+    __syncwarp();
+}
+
 template <int kMin, int kMax>
 __global__ void __launch_bounds__(kTeamWarps * 32, team_blocks<kMax>())
-    k_team_self(Geometry g, const int64_t* __restrict__ list, const int* __restrict__ n_list,
-                const float4* __restrict__ sorted, int* __restrict__ parent, int* err)
+    k_team_self(Geometry g, const int64_t* __restrict__ list, const int* __restrict__ n_list, float4* sorted,
+                int* __restrict__ parent, int* __restrict__ minorig, int* err)
 {
     constexpr int kTeamMax = kMax;
     constexpr int kTeamWords = kMax / 32;
@@ -511,6 +595,20 @@ __global__ void __launch_bounds__(kTeamWarps * 32, team_blocks<kMax>())
             continue;
         const BoxDev& b = g.boxes[box_of(g.box_p0, g.nbox, c0)];
 
+        // the cell in z order, also in global memory: the streams of the
+        // neighbours below then read only a z-prefix of it (k_link), and
+        // blocks of 32 here are z-slabs whose gaps prune block pairs.  No
+        // kernel has read these slots' order yet (cross-cell links come later).
+        // Cells below kSortMin are not sorted (k_link searches no smaller).
+        if (m >= kSortMin) {
+            sort_cell_z<kMax>(S, nw, lane);
+            for (int k = lane; k < m; k += 32) {
+                const float4 q = S.P[k];
+                sorted[c0 + k] = q;
+                minorig[c0 + k] = __float_as_int(q.w);
+            }
+        }
+
         // adjacency rows (row1: the only word when nw == 1)
         unsigned row1 = 0u;
         for (int ib = 0; ib < nw; ++ib) {
@@ -519,7 +617,14 @@ __global__ void __launch_bounds__(kTeamWarps * 32, team_blocks<kMax>())
             for (int jb = ib; jb < nw; ++jb) {
                 const int jn8 = (min(32, m - jb * 32) + 7) & ~7;
                 unsigned row;
-                if (b.nc >= 3) {
+                // z-slabs of a sorted cell too far apart: every pair's float32
+                // separation squared exceeds t_hi (rounding is monotone), so no link
+                const float gap = jb > ib && m >= kSortMin ? __fsub_rn(S.P[jb * 32].z, S.P[ib * 32 + 31].z) : 0.f;
+                if (b.nc >= 3 && gap > 0.f && __fmul_rn(gap, gap) > b.t_hi) {
+                    row = 0u;
+                    if (lane < min(32, m - jb * 32))
+                        S.adj[(jb * 32 + lane) * kAdjStride + ib] = 0u;
+                } else if (b.nc >= 3) {
                     row = jb == ib ? block_tests<kMax, false, false>(pi, S, jb, ib, jn8, lane, b)
                                    : block_tests<kMax, true, false>(pi, S, jb, ib, jn8, lane, b);
                 } else {
@@ -636,11 +741,11 @@ cudaError_t launch_team_self(const Geometry& g, const Work& w, cudaStream_t s)
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
     k_team_self<0, 128><<<sm_count() * team_blocks<128>(), kTeamWarps * 32, team_smem_bytes<128>(), s>>>(
-        g, w.team_list, w.n_team, w.sorted, w.parent, &w.status->err);
+        g, w.team_list, w.n_team, w.sorted, w.parent, w.minorig, &w.status->err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_team_self<128, kTeamSelfMax><<<sm_count() * team_blocks<kTeamSelfMax>(), kTeamWarps * 32, team_smem_bytes<kTeamSelfMax>(), s>>>(
-        g, w.team_list, w.n_team, w.sorted, w.parent, &w.status->err);
+        g, w.team_list, w.n_team, w.sorted, w.parent, w.minorig, &w.status->err);
     return cudaGetLastError();
 }
 

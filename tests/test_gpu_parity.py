@@ -370,3 +370,41 @@ def test_phase_timing_and_launch_count(cuda_lib):
         assert fof.fof_kernel_launches(h) == 2 * per_run
     finally:
         fof.fof_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# team cells in z order: block pairs pruned by their z gap, neighbour streams
+# cut to a z-prefix (cells sorted by k_team_self, searched in k_link)
+# --------------------------------------------------------------------------
+
+def _layered_cells(seed, nc=8, box=8.0, n_bg=3000, n_cells=40):
+    rng = np.random.default_rng(seed)
+    h = box / nc
+    parts = [rng.uniform(0.0, box, size=(n_bg, 3))]
+    cells = rng.integers(0, nc, size=(n_cells, 3))
+    cells[:8, 2] = nc - 1                      # some at the top row: wrap to z = 0
+    for c in cells:
+        m = int(rng.integers(20, 240))          # both sides of the 32-particle sort threshold
+        layers = rng.choice([0.03, 0.3, 0.6, 0.97], size=int(rng.integers(2, 5)), replace=False)
+        lay = layers[rng.integers(0, len(layers), size=m)]
+        p = np.empty((m, 3))
+        p[:, 0] = (c[0] + rng.uniform(0.0, 1.0, m)) * h
+        p[:, 1] = (c[1] + rng.uniform(0.0, 1.0, m)) * h
+        p[:, 2] = (c[2] + np.clip(lay + rng.normal(0.0, 0.01, m), 0.0, 0.999)) * h
+        parts.append(p)
+    pos = np.concatenate(parts) % box
+    pos = pos.astype(np.float32)
+    pos[pos >= np.float32(box)] = 0.0
+    return pos[rng.permutation(pos.shape[0])]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_zsorted_team_cells(cuda_lib, seed):
+    box, l_x = 8.0, 0.3
+    pos = _layered_cells(seed)
+    want = oracle.groups(pos, box, l_x)
+    opt = cuda_lib.fof_options()
+    opt.cells_per_axis = 8
+    opt.dense_min = 1 << 30                    # no sub-cells: every large cell is a team cell
+    assert_parity(cuda_lib, pos, box, l_x, 5, opt=opt, repeat=2, want=want)
+    assert_parity(cuda_lib, pos, box, l_x, 5, want=want)      # default cell grid
