@@ -406,7 +406,7 @@ struct TeamSmem {
 template <int kMax>
 constexpr int team_blocks()
 {
-    return 4;
+    return kMax <= 128 ? 5 : 4;
 }
 
 template <int kMax>
@@ -494,64 +494,34 @@ __device__ __forceinline__ void team_fetch(float4 (&R)[kMax / 32], int64_t e, co
 }
 
 // Sorts the staged cell (nw * 32 entries of S.P, sentinels after the cell's
-// particles) by z, exact float order: a bitonic network over 32-bit keys
-// (z >= 0, so the float bits order like the values) and their indices in the
-// adjacency area, which is free until the adjacency is built, then the
-// entries are permuted into place.
+// particles) by z in place: a bitonic network over the next power of two,
+// padded with more sentinels.  Every z is finite and non-negative, the
+// sentinels' z (kFar) exceeds every position, so the cell's particles come
+// first in exact float order.
 template <int kMax>
 __device__ __forceinline__ void sort_cell_z(TeamSmem<kMax>& S, int nw, int lane)
 {
     const int n = nw * 32;
     int n2 = 32;
     while (n2 < n) n2 <<= 1;                   // <= kMax
-    unsigned* key = S.adj;
-    unsigned short* id = reinterpret_cast<unsigned short*>(S.adj + kMax);
-    for (int k = lane; k < n2; k += 32) {
-        key[k] = k < n ? __float_as_uint(S.P[k].z) : 0xFFFFFFFFu;
-        id[k] = (unsigned short)k;
-    }
+    for (int k = n + lane; k < n2; k += 32)
+        S.P[k] = make_float4(kFar, kFar, kFar, 0.f);
     __syncwarp();
     for (int size = 2; size <= n2; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int i = lane; i < n2; i += 32) {
                 const int l = i ^ stride;
                 if (l > i) {
-                    const unsigned ki = key[i], kl = key[l];
-                    if ((ki > kl) == ((i & size) == 0)) {
-                        key[i] = kl;
-                        key[l] = ki;
-                        const unsigned short t = id[i];
-                        id[i] = id[l];
-                        id[l] = t;
+                    const float4 a = S.P[i], c = S.P[l];
+                    if ((a.z > c.z) == ((i & size) == 0)) {
+                        S.P[i] = c;
+                        S.P[l] = a;
                     }
                 }
             }
             __syncwarp();
         }
     }
-    if constexpr (kMax <= 128) {
-        // through registers: every read before any write
-        float4 v[kMax / 32];
-#pragma unroll
-        for (int r = 0; r < kMax / 32; ++r)
-            if (lane + 32 * r < n)
-                v[r] = S.P[id[lane + 32 * r]];
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < kMax / 32; ++r)
-            if (lane + 32 * r < n)
-                S.P[lane + 32 * r] = v[r];
-    } else {
-        // through a copy in the rest of the adjacency area
-        static_assert(kMax + kMax / 2 + 4 * kMax <= kMax * TeamSmem<kMax>::kStride, "scratch");
-        float4* copy = reinterpret_cast<float4*>(S.adj + kMax + kMax / 2);
-        for (int k = lane; k < n; k += 32)
-            copy[k] = S.P[k];
-        __syncwarp();
-        for (int k = lane; k < n; k += 32)
-            S.P[k] = copy[id[k]];
-    }
-    __syncwarp();
 }
 
 template <int kMin, int kMax>
