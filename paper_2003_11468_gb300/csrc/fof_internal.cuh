@@ -58,6 +58,11 @@ constexpr int kDenseMax = 3072;   // particles of a subdivided cell (shared memo
 // Largest team cell whose own pairs one warp links in shared memory
 // (k_team_self); larger unsplit cells link their own pairs in k_link.
 constexpr int kTeamSelfMax = 256;
+// Team cells from this size on (more than one warp word) are stored in z
+// order by k_team_self, and the kernels that stream them from the cell below
+// or above read only the z-prefix or suffix that can pair; sorting the many
+// small cells costs more than it saves.
+constexpr int kSortMin = 33;
 constexpr int kMaxQ = 12;
 constexpr int kMaxQ3 = kMaxQ * kMaxQ * kMaxQ;
 

@@ -80,12 +80,6 @@ __device__ __forceinline__ unsigned reach_mask(const float4& p, const BoxDev& b,
     return (hz ? m9 : 0u) | (hy ? xm << 9 : 0u) | (hx << 12);
 }
 
-// Team cells from this size on (more than one warp word) are stored in z
-// order (k_team_self) and their z-prefix searched by the streams of the
-// cells below them (k_link); sorting the many small cells costs more than it
-// saves.
-constexpr int kSortMin = 33;
-
 __device__ __forceinline__ float4 shfl4(float4 v, int src)
 {
     v.x = __shfl_sync(kFull, v.x, src);
