@@ -503,14 +503,15 @@ __device__ __forceinline__ void sort_cell_z(TeamSmem<kMax>& S, int nw, int lane)
     __syncwarp();
     for (int size = 2; size <= n2; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < n2; i += 32) {
-                const int l = i ^ stride;
-                if (l > i) {
-                    const float4 a = S.P[i], c = S.P[l];
-                    if ((a.z > c.z) == ((i & size) == 0)) {
-                        S.P[i] = c;
-                        S.P[l] = a;
-                    }
+            // pair p: its lower index i is p with a zero inserted at the
+            // stride bit, so every lane has a pair and accesses stay dense
+            for (int pr = lane; pr < (n2 >> 1); pr += 32) {
+                const int i = ((pr & ~(stride - 1)) << 1) | (pr & (stride - 1));
+                const int l = i | stride;
+                const float4 a = S.P[i], c = S.P[l];
+                if ((a.z > c.z) == ((i & size) == 0)) {
+                    S.P[i] = c;
+                    S.P[l] = a;
                 }
             }
             __syncwarp();
