@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
 // per-brick cell sort
 // ------------------------------------------------------------------------
 
-constexpr int kSortThreads = 512;
+constexpr int kSortThreads = 1024;
 constexpr int kMaxR3 = 4096;   // r <= 16
 
 __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const float4* __restrict__ tmp,
