@@ -78,7 +78,10 @@ typedef struct {
     int32_t size;    /* number of members                                */
 } fof_group;
 
-/* Tuning knobs; a zero field selects the library's default. */
+/* Tuning knobs and method variants; a zero field selects the library's
+ * default.  The variant fields exist to measure the paper's alternatives
+ * against the default; every variant gives the same partition (exactly),
+ * except tie_rule, which changes the graph at distance exactly l_x. */
 typedef struct {
     int32_t cells_per_axis;  /* cells per box side; must keep side >= l_x   */
     int32_t brick_cells;     /* cells per brick side: 1, 2, 4, 8 or 16      */
@@ -87,9 +90,55 @@ typedef struct {
                                 into sub-cells and linked in shared memory
                                 (default 256)                                */
     int32_t retry_cap;       /* max CAS attempts per union (default 2^20)    */
-    int32_t reserved[4];     /* [0]: occupancy from which a warp links a cell
-                                as a team (default 4); others must be 0      */
+    int32_t team_min;        /* cell occupancy from which one warp links the
+                                cell's particles as a team (default 4, >= 2) */
+    int32_t tie_rule;        /* FOF_TIE_LE (0, default): linked iff the
+                                distance is <= l_x (graph definition, Sec. 1
+                                footnote; "at most", abstract); FOF_TIE_LT:
+                                < l_x (the naive listing, Sec. 3.1)          */
+    int32_t find_variant;    /* FOF_FIND_*: path compression of Find
+                                (Sec. 3.4.3); default FOF_FIND_HALVE_DEEP    */
+    int32_t size_count;      /* FOF_SIZE_*: how group sizes are counted
+                                (Sec. 3.4.1); default FOF_SIZE_WARP          */
+    int32_t link_order;      /* FOF_LINK_*: which root a Union hooks
+                                (Sec. 3.1; Sec. 3.2); default FOF_LINK_MIN   */
+    int32_t debug_flags;     /* FOF_DEBUG_* bits; 0 in production            */
+    int32_t reserved[2];     /* must be 0                                    */
 } fof_options;
+
+/* tie_rule */
+enum { FOF_TIE_LE = 0, FOF_TIE_LT = 1 };
+/* find_variant: path compression during Find (Sec. 3.4.3) */
+enum {
+    FOF_FIND_HALVE_DEEP = 0, /* path halving, writing only where the path is at
+                                least 2 deep (the paper's choice)            */
+    FOF_FIND_HALVE_ALL = 1,  /* path halving at every depth (also rewrites the
+                                parent of a depth-1 node with its own value) */
+    FOF_FIND_FULL = 2,       /* full compression: a second pass points every
+                                node of the path at the root                 */
+    FOF_FIND_NONE = 3        /* no compression                               */
+};
+/* size_count: group sizes (Sec. 3.4.1, 3.4.2; roots never counted) */
+enum {
+    FOF_SIZE_WARP = 0,       /* equal roots aggregated per warp, one atomic each */
+    FOF_SIZE_HASH = 1        /* per-block shared-memory hash table of (root,
+                                count), flushed with one atomic per entry    */
+};
+/* link_order: which root Union hooks onto which */
+enum {
+    FOF_LINK_MIN = 0,        /* the larger root onto the smaller (union by root
+                                onto the lower offset, Sec. 3.1)             */
+    FOF_LINK_RANDOM = 1      /* randomised linking: the root of lower random
+                                priority onto the other (Jayanti and Tarjan,
+                                discussed in Sec. 3.2); the min-index labels
+                                are then set by the label pass               */
+};
+/* debug_flags */
+enum {
+    FOF_DEBUG_UNION_NO_RETRY = 1  /* every Union that must hook gives up at
+                                     once and reports FOF_ERR_TIMEOUT: a
+                                     deterministic test of the retry cap     */
+};
 
 /* ---------------------------------------------------------------------- */
 /* single box                                                              */

@@ -48,6 +48,12 @@ def _load():
             i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int32
             lib.fof_oracle_linked.argtypes = [P, P, f64, f64]
             lib.fof_oracle_linked.restype = ctypes.c_int
+            lib.fof_oracle_linked_rule.argtypes = [P, P, f64, f64, ctypes.c_int]
+            lib.fof_oracle_linked_rule.restype = ctypes.c_int
+            lib.fof_oracle_groups_rule.argtypes = [i64, P, f64, f64, ctypes.c_int, P, P]
+            lib.fof_oracle_groups_rule.restype = ctypes.c_int
+            lib.fof_oracle_brute_rule.argtypes = [i64, P, f64, f64, ctypes.c_int, P]
+            lib.fof_oracle_brute_rule.restype = ctypes.c_int
             lib.fof_oracle_linked_many.argtypes = [i64, P, P, f64, f64, P]
             lib.fof_oracle_linked_many.restype = None
             lib.fof_oracle_groups.argtypes = [i64, P, f64, f64, P, P]
@@ -73,10 +79,12 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def linked(a, b, box: float, l_x: float) -> bool:
-    """The exact link predicate for two float32 points."""
+def linked(a, b, box: float, l_x: float, strict: bool = False) -> bool:
+    """The exact link predicate for two float32 points (strict: distance < l_x)."""
     pa = np.ascontiguousarray(a, dtype=np.float32).reshape(3)
     pb = np.ascontiguousarray(b, dtype=np.float32).reshape(3)
+    if strict:
+        return bool(_load().fof_oracle_linked_rule(_ptr(pa), _ptr(pb), float(box), float(l_x), 1))
     return bool(_load().fof_oracle_linked(_ptr(pa), _ptr(pb), float(box), float(l_x)))
 
 
@@ -88,24 +96,31 @@ def linked_many(a, b, box: float, l_x: float) -> np.ndarray:
     return out.astype(bool)
 
 
-def groups(pos, box: float, l_x: float):
-    """(ids, sizes): min-index labels and per-label sizes, int32 arrays of n."""
+def groups(pos, box: float, l_x: float, strict: bool = False):
+    """(ids, sizes): min-index labels and per-label sizes, int32 arrays of n.
+    strict: link only pairs at distance < l_x (the naive listing's tie rule)."""
     p = _pos(pos)
     n = p.shape[0]
     ids = np.empty(n, dtype=np.int32)
     sizes = np.empty(n, dtype=np.int32)
-    rc = _load().fof_oracle_groups(n, _ptr(p), float(box), float(l_x), _ptr(ids), _ptr(sizes))
+    if strict:
+        rc = _load().fof_oracle_groups_rule(n, _ptr(p), float(box), float(l_x), 1, _ptr(ids), _ptr(sizes))
+    else:
+        rc = _load().fof_oracle_groups(n, _ptr(p), float(box), float(l_x), _ptr(ids), _ptr(sizes))
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
     return ids, sizes
 
 
-def brute(pos, box: float, l_x: float) -> np.ndarray:
+def brute(pos, box: float, l_x: float, strict: bool = False) -> np.ndarray:
     """ids by the O(N^2) pair loop with serial union-find (tiny inputs only)."""
     p = _pos(pos)
     n = p.shape[0]
     ids = np.empty(n, dtype=np.int32)
-    _load().fof_oracle_brute(n, _ptr(p), float(box), float(l_x), _ptr(ids))
+    if strict:
+        _load().fof_oracle_brute_rule(n, _ptr(p), float(box), float(l_x), 1, _ptr(ids))
+    else:
+        _load().fof_oracle_brute(n, _ptr(p), float(box), float(l_x), _ptr(ids))
     return ids
 
 

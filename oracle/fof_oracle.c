@@ -24,7 +24,9 @@
  * abstract and the <= of the graph definition decide the tie.
  * This file must be compiled with -ffp-contract=off (and no -ffast-math).
  *
- * Entry points:
+ * Entry points (the *_rule variants take the tie rule: strict = 1 links
+ * only pairs at distance < l_x, the naive listing's test in Sec. 3.1; the
+ * others use <=):
  *   fof_oracle_linked      the predicate itself (for pinning tests)
  *   fof_oracle_linked_many the predicate over arrays of pairs
  *   fof_oracle_groups      cell list + breadth-first search, all particles
@@ -51,7 +53,10 @@ static double wrap_axis(double d, double box)
     return d;
 }
 
-static int linked(const float *a, const float *b, double box, double l2)
+/* strict = 0: linked iff s <= l2 (the graph definition); strict = 1:
+ * linked iff s < l2, the "r < l_x" of the paper's naive pair loop (Sec. 3.1),
+ * kept to measure the tie rule as a variant. */
+static int linked_rule(const float *a, const float *b, double box, double l2, int strict)
 {
     double dx = wrap_axis((double)a[0] - (double)b[0], box);
     double dy = wrap_axis((double)a[1] - (double)b[1], box);
@@ -61,13 +66,26 @@ static int linked(const float *a, const float *b, double box, double l2)
     double zz = dz * dz;
     double s = xx + yy;
     s = s + zz;
+    if (strict)
+        return s < l2;
     return s <= l2;
+}
+
+static int linked(const float *a, const float *b, double box, double l2)
+{
+    return linked_rule(a, b, box, l2, 0);
 }
 
 int fof_oracle_linked(const float *a, const float *b, double box, double l_x)
 {
     double l2 = l_x * l_x;
     return linked(a, b, box, l2);
+}
+
+int fof_oracle_linked_rule(const float *a, const float *b, double box, double l_x, int strict)
+{
+    double l2 = l_x * l_x;
+    return linked_rule(a, b, box, l2, strict);
 }
 
 /* out[k] = the predicate for the pair (a[k], b[k]), k < m */
@@ -87,6 +105,7 @@ typedef struct {
     int64_t n;
     const float *pos;
     double box, l2;
+    int strict;          /* tie rule, see linked_rule */
     int64_t nc;          /* cells per axis */
     uint64_t *key;       /* key[k] of the k-th particle in cell order */
     int32_t *idx;        /* idx[k] = particle index */
@@ -127,10 +146,10 @@ static int64_t cells_per_axis(double box, double l_x)
     return (int64_t)q;
 }
 
-static int grid_build(grid_t *g, int64_t n, const float *pos, double box, double l_x)
+static int grid_build(grid_t *g, int64_t n, const float *pos, double box, double l_x, int strict)
 {
     memset(g, 0, sizeof(*g));
-    g->n = n; g->pos = pos; g->box = box; g->l2 = l_x * l_x;
+    g->n = n; g->pos = pos; g->box = box; g->l2 = l_x * l_x; g->strict = strict;
     g->nc = cells_per_axis(box, l_x);
     if (n == 0)
         return 0;
@@ -215,7 +234,7 @@ static int64_t bfs(const grid_t *g, int64_t start, int32_t label,
                 int32_t j = g->idx[k];
                 if (mark[j] == label)
                     continue;
-                if (linked(pp, g->pos + 3 * (int64_t)j, g->box, g->l2)) {
+                if (linked_rule(pp, g->pos + 3 * (int64_t)j, g->box, g->l2, g->strict)) {
                     mark[j] = label;
                     queue[tail++] = j;
                 }
@@ -232,13 +251,13 @@ static int64_t bfs(const grid_t *g, int64_t start, int32_t label,
 /* ids[i] = smallest index in i's group; sizes[g] = size of the group
  * labelled g, 0 where g is not a label.  Returns 0, or -1 on allocation
  * failure. */
-int fof_oracle_groups(int64_t n, const float *pos, double box, double l_x,
-                      int32_t *ids, int32_t *sizes)
+int fof_oracle_groups_rule(int64_t n, const float *pos, double box, double l_x, int strict,
+                           int32_t *ids, int32_t *sizes)
 {
     if (n == 0)
         return 0;
     grid_t g;
-    if (grid_build(&g, n, pos, box, l_x))
+    if (grid_build(&g, n, pos, box, l_x, strict))
         return -1;
     int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     if (!queue) { grid_free(&g); return -1; }
@@ -256,6 +275,12 @@ int fof_oracle_groups(int64_t n, const float *pos, double box, double l_x,
     return 0;
 }
 
+int fof_oracle_groups(int64_t n, const float *pos, double box, double l_x,
+                      int32_t *ids, int32_t *sizes)
+{
+    return fof_oracle_groups_rule(n, pos, box, l_x, 0, ids, sizes);
+}
+
 /* ------------------------------------------------------------------ */
 /* brute force: the paper's naive all-pairs union-find                 */
 /* ------------------------------------------------------------------ */
@@ -270,14 +295,15 @@ static int32_t uf_find(int32_t *parent, int32_t x)
 /* Every unordered pair i != j is tested; linked pairs merge their roots,
  * the larger root is hooked onto the smaller (Sec. 3.1), so the final root
  * of each set is its smallest index.  ids[i] = that root. */
-int fof_oracle_brute(int64_t n, const float *pos, double box, double l_x, int32_t *ids)
+int fof_oracle_brute_rule(int64_t n, const float *pos, double box, double l_x, int strict,
+                          int32_t *ids)
 {
     double l2 = l_x * l_x;
     for (int64_t i = 0; i < n; ++i)
         ids[i] = (int32_t)i;
     for (int64_t i = 0; i < n; ++i)
         for (int64_t j = i + 1; j < n; ++j) {
-            if (!linked(pos + 3 * i, pos + 3 * j, box, l2))
+            if (!linked_rule(pos + 3 * i, pos + 3 * j, box, l2, strict))
                 continue;
             int32_t ri = uf_find(ids, (int32_t)i);
             int32_t rj = uf_find(ids, (int32_t)j);
@@ -287,6 +313,11 @@ int fof_oracle_brute(int64_t n, const float *pos, double box, double l_x, int32_
     for (int64_t i = 0; i < n; ++i)
         ids[i] = uf_find(ids, (int32_t)i);
     return 0;
+}
+
+int fof_oracle_brute(int64_t n, const float *pos, double box, double l_x, int32_t *ids)
+{
+    return fof_oracle_brute_rule(n, pos, box, l_x, 0, ids);
 }
 
 /* ------------------------------------------------------------------ */
@@ -301,7 +332,7 @@ int fof_oracle_component(int64_t n, const float *pos, double box, double l_x,
                          int64_t *label)
 {
     grid_t g;
-    if (grid_build(&g, n, pos, box, l_x))
+    if (grid_build(&g, n, pos, box, l_x, 0))
         return -1;
     int32_t *mark = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     if (!mark) { grid_free(&g); return -1; }

@@ -88,27 +88,6 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src)
     return v;
 }
 
-// Unions found in one chunk, done lane-parallel: `links` holds, per lane,
-// the candidates (lane indices of the chunk) it is linked to; every round
-// each lane with a pending link merges with that candidate's root snapshot
-// `rj`, so the chunk waits for as many union latencies as its busiest lane
-// has links, not one per linked candidate.  A snapshot root equal to the
-// lane's current or last merged root needs nothing (groups only merge).
-__device__ __forceinline__ void chunk_unions(int* parent, unsigned links, int rj, int& ri, int& last,
-                                             int cap, int* err)
-{
-    while (__any_sync(kFull, links != 0u)) {
-        const bool has = links != 0u;
-        const int u = has ? __ffs(links) - 1 : 0;
-        links &= links - 1u;
-        const int rt = __shfl_sync(kFull, rj, u);
-        if (has && rt != ri && rt != last) {
-            ri = uf_union(parent, ri, rt, cap, err);
-            last = rt;
-        }
-    }
-}
-
 // Bounding box of the team's particles.
 struct TeamBox {
     float lx, ly, lz, hx, hy, hz;
@@ -126,97 +105,96 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
-// One warp links the lanes with `act` (all in one cell of box b) against
-// the candidates in [j0, j1).  `own` = the candidates lie in the own cell,
-// so lane i only takes j > its slot.  Otherwise (filter = true) a candidate
-// farther than bb_reach2 (squared, float32) from the team's bounding box,
-// after the periodic shift (sx, sy, sz) of its cell, is dropped before any
-// root lookup: bb_reach2 covers l_x plus the float32 rounding of the shift
-// and of the gap (setup_box), so no linked pair is dropped.
-__device__ __forceinline__ void team_link(int* __restrict__ parent, const float4* __restrict__ sorted,
-                                          const BoxDev& b, bool act, int64_t s, const float4& p,
-                                          int& ri, int& last, int j0, int j1, bool own, bool filter,
-                                          const TeamBox& tb, float sx, float sy, float sz, int cap,
-                                          int* err)
+__device__ __forceinline__ unsigned lanemask_lt()
 {
-    const int lane = threadIdx.x & 31;
-    const int ref_lane = __ffs(__ballot_sync(kFull, act)) - 1;
-    for (int jb = j0; jb < j1; jb += kWarp) {
-        int j = jb + lane;
-        bool jv = j < j1;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (jv) {
-            q = sorted[j];
-            if (filter) {
-                float x = q.x + sx, y = q.y + sy, z = q.z + sz;
-                float gx = fmaxf(0.f, fmaxf(tb.lx - x, x - tb.hx));
-                float gy = fmaxf(0.f, fmaxf(tb.ly - y, y - tb.hy));
-                float gz = fmaxf(0.f, fmaxf(tb.lz - z, z - tb.hz));
-                jv = gx * gx + gy * gy + gz * gz <= b.bb_reach2;
-            }
-        }
-        unsigned cand = __ballot_sync(kFull, jv);
-        if (!cand)
-            continue;
-        const int rj = jv ? uf_find(parent, j, err) : -1;
-        // chunk skip: every root on both sides equal to one value
-        const int ref = __shfl_sync(kFull, ri, ref_lane);
-        if (__all_sync(kFull, (!act || ri == ref) && (!jv || rj == ref)))
-            continue;
-        unsigned links = 0u;
-        while (cand) {
-            const int t = __ffs(cand) - 1;
-            cand &= cand - 1;
-            const int rt = __shfl_sync(kFull, rj, t);
-            const float4 qt = shfl4(q, t);
-            // rt == last: this lane already merged with that group
-            const bool need = act && ri != rt && rt != last && (!own || jb + t > s);
-            if (!__any_sync(kFull, need))
-                continue;
-            if (need && linked(p, qt, b))
-                links |= 1u << t;
-        }
-        chunk_unions(parent, links, rj, ri, last, cap, err);
-    }
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
 }
 
-// The reachable forward neighbours of a team's cell as ONE stream of
-// candidates, 32 per step: lane k < 13 holds neighbour k's first slot (j0k)
-// and the number of its particles to visit (cntk, 0 when the team does not
-// reach it).  Each candidate keeps its neighbour index, which gives its
-// periodic shift for the box filter and the lanes that reach it.
-__device__ __forceinline__ void team_stream(int* __restrict__ parent, const float4* __restrict__ sorted,
-                                            const BoxDev& b, bool mine, unsigned reach, const float4& p,
-                                            int& ri, int& last, const Cell& tc, int j0k, int cntk,
-                                            const TeamBox& tb, bool filter, int cap, int* err)
+// Inclusive warp prefix sum.
+__device__ __forceinline__ int warp_incl(int v, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    int x = cntk;
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
+        int y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += y;
     }
-    const int start_k = x - cntk;
-    const int total = __shfl_sync(kFull, x, 31);
-    const int ref_lane = __ffs(__ballot_sync(kFull, mine)) - 1;
-    for (int base = 0; base < total; base += kWarp) {
-        const int t = base + lane;
-        bool jv = t < total;
-        int lo = 0, hi = 12;                   // last neighbour whose stream starts at or before t
+    return v;
+}
+
+// Last lane l with start(l) <= t, where `start` is a non-decreasing per-lane
+// value with start(0) == 0 <= t (a binary search over the lanes; lanes
+// with an empty range share their successor's start and are never chosen).
+__device__ __forceinline__ int owner_lane(int start, int t)
+{
+    int lo = 0;
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-            int mid = (lo + hi + 1) >> 1;
-            int sm = __shfl_sync(kFull, start_k, mid);
-            if (lo < hi) {
-                if (sm <= t) lo = mid; else hi = mid - 1;
-            }
+    for (int step = 16; step; step >>= 1) {      // lo + step <= 31 throughout
+        const int probe = __shfl_sync(kFull, start, lo + step);
+        if (probe <= t) lo += step;
+    }
+    return lo;
+}
+
+// The index of the r-th (0-based) set bit of m (r < popc(m)).
+__device__ __forceinline__ int nth_bit(unsigned m, int r)
+{
+    for (; r > 0; --r) m &= m - 1u;
+    return __ffs(m) - 1;
+}
+
+// Per-warp staging of the team path: the team's members and one chunk of
+// compacted candidates, in shared memory.
+struct TeamStage {
+    float4 mpos[32];    // member a = lane lo + a of the team: x, y, z, w = reach mask bits
+    float4 cpos[32];    // candidate b of the chunk: x, y, z, w = neighbour index (13 = own cell)
+    int mroot[32];      // a root of member a (possibly stale: equal roots prove one group)
+    int croot[32];      // root snapshot of candidate b
+    int cslot[32];      // slot of candidate b
+    unsigned lmask[32]; // candidates of the chunk member a is linked to
+};
+
+constexpr int kLinkThreads = 256;
+constexpr int kLinkWarps = kLinkThreads / 32;
+constexpr int kOwnCell = 13;     // stream index of a team's own cell (cells above kTeamSelfMax)
+
+// One team cell: its members (lanes lo .. lo+m-1 of the warp, contiguous
+// slots first .. first+m-1) against every particle they can reach in the
+// forward neighbour cells, as ONE stream of candidates, 32 per chunk.
+// Lane k < 13 holds neighbour k's first slot and count (0 when the team does
+// not reach it or the dense kernels own it); lane 13 the rest of the own
+// cell when the cell is larger than kTeamSelfMax (k_team_self links the own
+// pairs of smaller cells).  Per chunk:
+//   * candidates outside the team's bounding box + l_x are dropped;
+//   * the chunk is skipped when all roots (members and candidates) agree,
+//     which is exact because groups only merge;
+//   * the survivors are compacted into shared memory and the m x c pairs
+//     are tested lane-parallel (one pair per lane and step), skipping pairs
+//     whose roots already agree; linked pairs set bits in the member's link
+//     mask;
+//   * each member then merges with the distinct candidate roots it links to.
+__device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent,
+                                          const float4* __restrict__ sorted, const BoxDev& b, int lane,
+                                          int lo, int m, int first, const Cell& tc, int j0k, int cntk,
+                                          const TeamBox& tb, bool filter, int cap, int* err)
+{
+    const int start_k = warp_incl(cntk, lane) - cntk;
+    const int total = __shfl_sync(kFull, start_k + cntk, 31);
+    for (int cb = 0; cb < total; cb += kWarp) {
+        const int t = cb + lane;
+        bool jv = t < total;
+        int k = 0;                              // last stream entry starting at or before t
+#pragma unroll
+        for (int step = 8; step; step >>= 1) {
+            const int probe = k + step <= 13 ? k + step : 13;
+            const int sm = __shfl_sync(kFull, start_k, probe);
+            if (k + step <= 13 && sm <= t) k += step;
         }
-        const int k = lo;
         const int j = __shfl_sync(kFull, j0k, k) + (t - __shfl_sync(kFull, start_k, k));
         float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
         if (jv) {
             q = sorted[j];
-            if (filter) {
+            if (filter && k < kOwnCell) {
                 int dx, dy, dz;
                 fwd_offset(k, dx, dy, dz);
                 const float sx = tc.cx + dx < 0 ? -b.Lf : (tc.cx + dx >= b.nc ? b.Lf : 0.f);
@@ -229,38 +207,77 @@ __device__ __forceinline__ void team_stream(int* __restrict__ parent, const floa
                 jv = gx * gx + gy * gy + gz * gz <= b.bb_reach2;
             }
         }
-        unsigned cand = __ballot_sync(kFull, jv);
+        const unsigned cand = __ballot_sync(kFull, jv);
         if (!cand)
             continue;
         const int rj = jv ? uf_find(parent, j, err) : -1;
-        const int ref = __shfl_sync(kFull, ri, ref_lane);
-        if (__all_sync(kFull, (!mine || ri == ref) && (!jv || rj == ref)))
+        const int ref = S.mroot[0];
+        const int mr = lane < m ? S.mroot[lane] : ref;
+        if (__all_sync(kFull, mr == ref && (!jv || rj == ref)))
             continue;
-        unsigned links = 0u;
-        while (cand) {
-            const int u = __ffs(cand) - 1;
-            cand &= cand - 1;
-            const int rt = __shfl_sync(kFull, rj, u);
-            const int kt = __shfl_sync(kFull, k, u);
-            const float4 qt = shfl4(q, u);
-            // rt == last: this lane already merged with that group
-            const bool need = mine && ((reach >> kt) & 1u) && ri != rt && rt != last;
-            if (!__any_sync(kFull, need))
-                continue;
-            if (need && linked(p, qt, b))
-                links |= 1u << u;
+        const int c = __popc(cand);
+        if (jv) {
+            const int r = __popc(cand & lanemask_lt());
+            S.cpos[r] = make_float4(q.x, q.y, q.z, __int_as_float(k));
+            S.croot[r] = rj;
+            S.cslot[r] = j;
         }
-        chunk_unions(parent, links, rj, ri, last, cap, err);
+        __syncwarp();
+        // pair t2 = a * c + bb, advanced by 32 per step without a division
+        const int P = m * c;
+        int a = lane / c;
+        int bb = lane - a * c;
+        const int qa = kWarp / c, qb = kWarp - qa * c;
+        for (int t2 = lane; t2 < P; t2 += kWarp) {
+            const float4 pm = S.mpos[a];
+            const float4 qc = S.cpos[bb];
+            const int kc = __float_as_int(qc.w);
+            bool need = kc == kOwnCell ? S.cslot[bb] > first + a : ((__float_as_int(pm.w) >> kc) & 1);
+            need = need && S.mroot[a] != S.croot[bb];
+            if (need && linked(pm, qc, b))
+                atomicOr(&S.lmask[a], 1u << bb);
+            bb += qb;
+            a += qa;
+            if (bb >= c) {
+                bb -= c;
+                ++a;
+            }
+        }
+        __syncwarp();
+        if (lane < m) {
+            unsigned links = S.lmask[lane];
+            if (links) {
+                int ri = S.mroot[lane];
+                int last = -1;
+                while (links) {
+                    const int u = __ffs(links) - 1;
+                    links &= links - 1u;
+                    const int rt = S.croot[u];
+                    if (rt != ri && rt != last) {
+                        ri = uf_union(parent, ri, rt, cap, err);
+                        last = rt;
+                    }
+                }
+                S.mroot[lane] = ri;
+                S.lmask[lane] = 0u;
+            }
+        }
+        __syncwarp();
     }
 }
 
-__global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restrict__ sorted,
-                                              const int* __restrict__ cell_start, int* parent,
-                                              int dense_min, int cap, int* err)
+__global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4* __restrict__ sorted,
+                                                       const int* __restrict__ cell_start, int* parent,
+                                                       int dense_min, int cap, int* err)
 {
+    __shared__ TeamStage stage[kLinkWarps];
     const int lane = threadIdx.x & 31;
+    TeamStage& S = stage[threadIdx.x >> 5];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (lane < 32)
+        S.lmask[lane] = 0u;
+    __syncwarp();
 
     for (int64_t base = warp * kWarp; base < g.total_n; base += nwarps * kWarp) {
         const int64_t s = base + lane;
@@ -282,24 +299,23 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
             c1 = cell_start[self + 1];
         }
         const bool sub = valid && is_sub(c1 - c0, g.boxes[bi], dense_min);
-        const bool dense = valid && !sub && (c1 - c0) >= g.boxes[bi].team_min;
-        unsigned dmask = __ballot_sync(kFull, dense);
+        const bool team = valid && !sub && (c1 - c0) >= g.boxes[bi].team_min;
+        unsigned tmask = __ballot_sync(kFull, team);
 
-        // ---- dense cells: the whole warp links each cell as a team ----
-        while (dmask) {
-            const int lead = __ffs(dmask) - 1;
+        // ---- team cells: the warp links each cell's members as a team ----
+        while (tmask) {
+            const int lead = __ffs(tmask) - 1;
             const int64_t key = __shfl_sync(kFull, self, lead);
-            const bool mine = dense && self == key;
+            const bool mine = team && self == key;
             const unsigned peers = __ballot_sync(kFull, mine);
-            dmask &= ~peers;
+            tmask &= ~peers;
+            const int m = __popc(peers);          // members: lanes lead .. lead + m - 1
             const int tbi = __shfl_sync(kFull, bi, lead);
             const BoxDev& b = g.boxes[tbi];
             Cell tc;
             tc.cx = __shfl_sync(kFull, c.cx, lead);
             tc.cy = __shfl_sync(kFull, c.cy, lead);
             tc.cz = __shfl_sync(kFull, c.cz, lead);
-            int ri = mine ? uf_find(parent, (int)s, err) : -1;
-            int last = -1;                    // root snapshot of this lane's last union
             const float inf = __int_as_float(0x7f800000);
             TeamBox tbx;
             tbx.lx = warp_min(mine ? p.x : inf);
@@ -308,26 +324,29 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
             tbx.hx = warp_max(mine ? p.x : -inf);
             tbx.hy = warp_max(mine ? p.y : -inf);
             tbx.hz = warp_max(mine ? p.z : -inf);
-            // own cell: linked by k_team_self unless the cell is larger
-            {
-                int first = (int)__shfl_sync(kFull, s, lead);
-                int end = __shfl_sync(kFull, c1, lead);
-                if (end - __shfl_sync(kFull, c0, lead) > kTeamSelfMax)
-                    team_link(parent, sorted, b, mine, s, p, ri, last, first + 1, end, true, false, tbx, 0.f,
-                              0.f, 0.f, cap, err);
-            }
             const unsigned reach = mine ? reach_mask(p, b, tc) : 0u;
             const unsigned team_reach = __reduce_or_sync(kFull, reach);
+            if (mine) {
+                S.mpos[lane - lead] = make_float4(p.x, p.y, p.z, __int_as_float((int)reach));
+                S.mroot[lane - lead] = uf_find(parent, (int)s, err);
+            }
+            const int first = (int)__shfl_sync(kFull, s, lead);
+            const int cell_end = __shfl_sync(kFull, c1, lead);
+            const int cell_size = cell_end - __shfl_sync(kFull, c0, lead);
             // lane k < 13: neighbour k's range, if the team reaches it and
-            // the dense kernels do not own it
+            // the dense kernels do not own it; lane 13: the own cell's
+            // particles after the first member, for cells k_team_self skips
             int j0k = 0, cntk = 0;
             if (lane < 13 && ((team_reach >> lane) & 1u) && !nbr_duplicate(b, tc, lane, key)) {
-                int64_t nk = nbr_key(b, tc, lane);
-                int j0 = cell_start[nk], j1 = cell_start[nk + 1];
+                const int64_t nk = nbr_key(b, tc, lane);
+                const int j0 = cell_start[nk], j1 = cell_start[nk + 1];
                 if (j1 > j0 && !is_sub(j1 - j0, b, dense_min)) {
                     j0k = j0;
                     cntk = j1 - j0;
                 }
+            } else if (lane == kOwnCell && cell_size > kTeamSelfMax) {
+                j0k = first + 1;
+                cntk = cell_end - first - 1;
             }
             // Neighbours k < 9 lie one cell up in z.  A team cell there (sorted
             // by z in k_team_self) is cut to the prefix that the box filter can
@@ -347,27 +366,71 @@ __global__ void __launch_bounds__(256) k_link(Geometry g, const float4* __restri
                 }
                 cntk = lo;
             }
-            team_stream(parent, sorted, b, mine, reach, p, ri, last, tc, j0k, cntk, tbx, b.nc >= 3, cap,
-                        err);
+            __syncwarp();
+            team_cell(S, parent, sorted, b, lane, lead, m, first, tc, j0k, cntk, tbx, b.nc >= 3, cap, err);
         }
 
-        // ---- sparse cells: every lane on its own ----
-        if (valid && !dense && !sub) {
+        // ---- sparse particles: their (particle, cell) items, then their
+        // (particle, candidate) pairs, pooled across the warp ----
+        const bool sparse = valid && !team && !sub;
+        unsigned reach_s = 0u;
+        int own_n = 0;
+        if (sparse) {
             const BoxDev& b = g.boxes[bi];
-            for (int j = (int)s + 1; j < c1; ++j)
-                if (linked(p, sorted[j], b))
-                    uf_union(parent, (int)s, j, cap, err);
-            const unsigned reach = reach_mask(p, b, c);
-            for (int k = 0; k < 13; ++k) {
-                if (!((reach >> k) & 1u) || nbr_duplicate(b, c, k, self))
-                    continue;
-                int64_t nk = nbr_key(b, c, k);
-                int j0 = cell_start[nk], j1 = cell_start[nk + 1];
-                if (is_sub(j1 - j0, b, dense_min))
-                    continue;
-                for (int j = j0; j < j1; ++j)
-                    if (linked(p, sorted[j], b))
-                        uf_union(parent, (int)s, j, cap, err);
+            reach_s = reach_mask(p, b, c);
+            if (b.nc < 3)
+                for (int k = 0; k < 13; ++k)
+                    if (((reach_s >> k) & 1u) && nbr_duplicate(b, c, k, self))
+                        reach_s &= ~(1u << k);
+            own_n = c1 - (int)s - 1;
+        }
+        const int nit = sparse ? (own_n > 0) + __popc(reach_s) : 0;
+        const int istart = warp_incl(nit, lane) - nit;
+        const int T = __shfl_sync(kFull, istart + nit, 31);
+        for (int ib = 0; ib < T; ib += kWarp) {
+            // item ib + lane: owner o, and its candidate range [j0, j0 + cnt)
+            const int t = ib + lane;
+            const bool iv = t < T;
+            const int o = owner_lane(istart, iv ? t : T - 1);
+            const int r = t - __shfl_sync(kFull, istart, o);
+            const int own_o = __shfl_sync(kFull, own_n, o);
+            const unsigned reach_o = __shfl_sync(kFull, reach_s, o);
+            const int obi = __shfl_sync(kFull, bi, o);
+            Cell oc;
+            oc.cx = __shfl_sync(kFull, c.cx, o);
+            oc.cy = __shfl_sync(kFull, c.cy, o);
+            oc.cz = __shfl_sync(kFull, c.cz, o);
+            int j0 = 0, cnt = 0;
+            if (iv) {
+                if (own_o > 0 && r == 0) {
+                    j0 = (int)(base + o) + 1;
+                    cnt = own_o;
+                } else {
+                    const BoxDev& b = g.boxes[obi];
+                    const int k = nth_bit(reach_o, r - (own_o > 0));
+                    const int64_t nk = nbr_key(b, oc, k);
+                    const int a0 = cell_start[nk], a1 = cell_start[nk + 1];
+                    if (!is_sub(a1 - a0, b, dense_min)) {
+                        j0 = a0;
+                        cnt = a1 - a0;
+                    }
+                }
+            }
+            const int cstart = warp_incl(cnt, lane) - cnt;
+            const int C = __shfl_sync(kFull, cstart + cnt, 31);
+            for (int cb = 0; cb < C; cb += kWarp) {
+                const int u = cb + lane;
+                const bool uv = u < C;
+                const int it = owner_lane(cstart, uv ? u : C - 1);
+                const int jj = __shfl_sync(kFull, j0, it) + (u - __shfl_sync(kFull, cstart, it));
+                const int oo = __shfl_sync(kFull, o, it);
+                const float4 po = shfl4(p, oo);
+                const int pbi = __shfl_sync(kFull, bi, oo);
+                if (uv) {
+                    const BoxDev& b = g.boxes[pbi];
+                    if (linked(po, sorted[jj], b))
+                        uf_union(parent, (int)(base + oo), jj, cap, err);
+                }
             }
         }
     }

@@ -116,6 +116,12 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
     if (!std::isfinite(L) || !(L > 0.0) || !std::isfinite(l_x) || !(l_x > 0.0) ||
         !(l_x < 0.5 * L) || n < 0 || n > kMaxTotal || L > 1e30)
         return FOF_ERR_ARG;
+    if (o && (o->tie_rule < 0 || o->tie_rule > FOF_TIE_LT || o->find_variant < 0 ||
+              o->find_variant > FOF_FIND_NONE || o->size_count < 0 || o->size_count > FOF_SIZE_HASH ||
+              o->link_order < 0 || o->link_order > FOF_LINK_RANDOM ||
+              (o->debug_flags & ~FOF_DEBUG_UNION_NO_RETRY) != 0 || o->reserved[0] != 0 ||
+              o->reserved[1] != 0 || o->team_min < 0 || o->dense_min < 0 || o->retry_cap < 0))
+        return FOF_ERR_ARG;
     std::memset(&b, 0, sizeof(b));
     double q = std::floor(L / (l_x * (1.0 + std::ldexp(1.0, -9))));
     int64_t nc_max = q < 1.0 ? 1 : (q > kMaxCellsPerAxis ? kMaxCellsPerAxis : (int64_t)q);
@@ -168,6 +174,11 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
     b.n = n;
     b.L = L;
     b.l2 = l_x * l_x;
+    // "distance < l_x" (the naive listing's test, Sec. 3.1): for doubles,
+    // s < l2 exactly when s <= the largest double below l2.  Every margin
+    // below is relative and far wider than this one step.
+    if (o && o->tie_rule == FOF_TIE_LT)
+        b.l2 = std::nextafter(b.l2, 0.0);
     b.nb = (int32_t)nb;
     b.r = r;
     b.log2r = log2r;
@@ -186,7 +197,7 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
         double rf = l_x / (L / (double)b.nf) + std::ldexp(1.0, -6);
         b.reach2 = (float)(rf * rf * (1.0 + std::ldexp(1.0, -20)));
     }
-    b.team_min = (o && o->reserved[0] > 0) ? o->reserved[0] : kDefaultTeamMin;
+    b.team_min = (o && o->team_min > 0) ? o->team_min : kDefaultTeamMin;
     if (b.team_min < kMinTeamMin)
         b.team_min = kMinTeamMin;
     // Team bounding-box filter.  A neighbour particle shifted by +-float32(L)
@@ -453,6 +464,8 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     h->boxes = boxes;
     if (opt && opt->dense_min > 0) h->dense_min = opt->dense_min;
     if (opt && opt->retry_cap > 0) h->retry_cap = opt->retry_cap;
+    // the retry-cap test: a union that must hook gives up before its first CAS
+    if (opt && (opt->debug_flags & FOF_DEBUG_UNION_NO_RETRY)) h->retry_cap = 0;
     h->rl = results_layout(nbox);
     if (workspace) {
         h->ws = (char*)workspace;

@@ -36,8 +36,21 @@ class fof_options(ctypes.Structure):
         ("occupancy", ctypes.c_double),
         ("dense_min", ctypes.c_int32),
         ("retry_cap", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("team_min", ctypes.c_int32),
+        ("tie_rule", ctypes.c_int32),
+        ("find_variant", ctypes.c_int32),
+        ("size_count", ctypes.c_int32),
+        ("link_order", ctypes.c_int32),
+        ("debug_flags", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
+
+
+FOF_TIE_LE, FOF_TIE_LT = 0, 1
+FOF_FIND_HALVE_DEEP, FOF_FIND_HALVE_ALL, FOF_FIND_FULL, FOF_FIND_NONE = 0, 1, 2, 3
+FOF_SIZE_WARP, FOF_SIZE_HASH = 0, 1
+FOF_LINK_MIN, FOF_LINK_RANDOM = 0, 1
+FOF_DEBUG_UNION_NO_RETRY = 1
 
 
 class fof_geometry(ctypes.Structure):

@@ -49,7 +49,7 @@ def options_from(d: dict | None) -> fof.fof_options | None:
     if "dense_min" in d:
         o.dense_min = int(d["dense_min"])
     if "team_min" in d:
-        o.reserved[0] = int(d["team_min"])
+        o.team_min = int(d["team_min"])
     if "brick_cells" in d:
         o.brick_cells = int(d["brick_cells"])
     return o

@@ -274,26 +274,38 @@ def test_state_and_capacity(cuda_lib):
 
 
 def test_retry_cap_exhaustion_reports_timeout(cuda_lib):
-    """A retry cap of one CAS attempt per union makes contended unions give
-    up; the library must report it instead of returning a wrong partition."""
+    """With FOF_DEBUG_UNION_NO_RETRY every Union gives up before its first
+    CAS, as a union that exhausted its retry cap does.  The 32^3 uniform box
+    has hundreds of linked pairs between sparse cells, so unions are certain
+    to be attempted: the library must report FOF_ERR_TIMEOUT, never a
+    partition.  The same plan options without the flag give the exact
+    answer."""
+    import oracle
     torch = _torch()
     fof = cuda_lib
-    same = np.tile(np.array([[0.5, 0.5, 0.5]], dtype=np.float32), (20000, 1))
-    opt = fof.fof_options()
-    opt.retry_cap = 1
-    h = fof.fof_create_ex(1.0, 0.01, 20000, opt)
-    try:
-        ids = torch.empty(20000, dtype=torch.int32, device="cuda")
-        sizes = torch.empty(20000, dtype=torch.int32, device="cuda")
-        fof.fof_link(h, torch.from_numpy(same).cuda())
+    c = synth.uniform_32k()
+    pos = c["make"]()
+    n = c["n"]
+    wid, _ = oracle.groups(pos, c["box"], c["l_x"])
+    assert (wid != np.arange(n)).any()            # some pairs are linked
+    dev = torch.from_numpy(pos).cuda()
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    sizes = torch.empty(n, dtype=torch.int32, device="cuda")
+    for flag in (fof.FOF_DEBUG_UNION_NO_RETRY, 0):
+        opt = fof.fof_options()
+        opt.debug_flags = flag
+        h = fof.fof_create_ex(c["box"], c["l_x"], n, opt)
         try:
-            code, ng, nk = fof.fof_groups(h, ids, sizes, None, 0, 1)
-            # no union needed a second attempt: then the answer is exact
-            assert (ids.cpu().numpy() == 0).all() and ng[0] == 1
-        except fof.FoFError as e:
-            assert e.code == fof.FOF_ERR_TIMEOUT
-    finally:
-        fof.fof_destroy(h)
+            fof.fof_link(h, dev)
+            if flag:
+                with pytest.raises(fof.FoFError) as e:
+                    fof.fof_groups(h, ids, sizes, None, 0, 1)
+                assert e.value.code == fof.FOF_ERR_TIMEOUT
+            else:
+                fof.fof_groups(h, ids, sizes, None, 0, 1)
+                assert np.array_equal(ids.cpu().numpy(), wid)
+        finally:
+            fof.fof_destroy(h)
 
 
 # --------------------------------------------------------------------------
@@ -408,3 +420,25 @@ def test_zsorted_team_cells(cuda_lib, seed):
     opt.dense_min = 1 << 30                    # no sub-cells: every large cell is a team cell
     assert_parity(cuda_lib, pos, box, l_x, 5, opt=opt, repeat=2, want=want)
     assert_parity(cuda_lib, pos, box, l_x, 5, want=want)      # default cell grid
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tie_rule_option(cuda_lib, seed):
+    """FOF_TIE_LT (distance < l_x, the naive listing of Sec. 3.1) against the
+    oracle's strict rule, on grid points where many pairs are exactly l_x
+    apart; the default rule on the same input for contrast."""
+    torch = _torch()
+    fof = cuda_lib
+    rng = np.random.default_rng(900 + seed)
+    n = 20000
+    g = 2.0 ** -5
+    pos = (rng.integers(0, 32, size=(n, 3)) * g).astype(np.float32)
+    dev = torch.from_numpy(pos).cuda()
+    for strict in (True, False):
+        opt = fof.fof_options()
+        opt.tie_rule = fof.FOF_TIE_LT if strict else fof.FOF_TIE_LE
+        with fof.FoF(1.0, g, n, opt) as f:
+            ids, sizes, _, _ = f.run(dev)
+        wid, wsz = oracle.groups(pos, 1.0, g, strict=strict)
+        assert np.array_equal(ids.cpu().numpy(), wid), strict
+        assert np.array_equal(sizes.cpu().numpy(), wsz), strict

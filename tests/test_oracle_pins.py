@@ -261,3 +261,87 @@ def test_catalogue_filter():
     cat = oracle.catalogue(sizes, 0)
     assert cat[:, 0].tolist() == [0, 3, 4, 6, 7]
     assert oracle.catalogue(sizes, 26).shape == (0, 2)
+
+
+# --------------------------------------------------------------------------
+# the strict tie rule (distance < l_x, the naive listing of Sec. 3.1) and the
+# array form of the predicate
+# --------------------------------------------------------------------------
+
+def test_strict_rule_on_tie_pairs():
+    """At distance exactly l_x the strict rule does not link; just above the
+    tie (the next double above l_x) it does, like the default rule."""
+    for r in read_rows("tie_pairs.txt"):
+        box = float(r[0])
+        a = np.array([float(v) for v in r[1:4]], dtype=np.float32)
+        b = np.array([float(v) for v in r[4:7]], dtype=np.float32)
+        l_x, want, exact = float(r[7]), int(r[8]), int(r[9])
+        if exact:
+            assert not oracle.linked(a, b, box, l_x, strict=True), r
+            assert oracle.linked(a, b, box, float(np.nextafter(l_x, 1.0)), strict=True), r
+        elif not want:
+            assert not oracle.linked(a, b, box, l_x, strict=True), r
+
+
+def test_strict_rule_lattice_closed_form():
+    """A lattice of spacing d: with l_x = d the strict rule leaves every point
+    alone (each neighbour is exactly d away), the default rule joins all."""
+    pos = _lattice(3)
+    d = 2.0 ** -3
+    ids, sizes = oracle.groups(pos, 1.0, d, strict=True)
+    assert np.array_equal(ids, np.arange(pos.shape[0])) and (sizes == 1).all()
+    ids, _ = oracle.groups(pos, 1.0, float(np.nextafter(d, 1.0)), strict=True)
+    assert (ids == 0).all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_strict_rule_groups_equal_brute(seed):
+    """Cell list + BFS under the strict rule equals the all-pairs loop."""
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(50, 600))
+    # points on a coarse grid so that many pairs sit exactly at l_x
+    g = 2.0 ** -4
+    pos = (rng.integers(0, 16, size=(n, 3)) * g).astype(np.float32)
+    ids, _ = oracle.groups(pos, 1.0, g, strict=True)
+    assert np.array_equal(ids, oracle.brute(pos, 1.0, g, strict=True))
+    ids_le, _ = oracle.groups(pos, 1.0, g)
+    assert np.array_equal(ids_le, oracle.brute(pos, 1.0, g))
+    # on this grid the two rules differ: exact ties join only under <=
+    assert not np.array_equal(ids, ids_le)
+
+
+def test_linked_many_equals_linked_on_adversarial_pairs():
+    """The array form of the predicate against the single-pair form, on pairs
+    at exact ties, one float step inside and outside l_x, across the periodic
+    wrap on every axis, and random pairs."""
+    rng = np.random.default_rng(11)
+    box, l_x = 1.0, 0.03125
+    a = []
+    b = []
+    for r in read_rows("tie_pairs.txt"):
+        if float(r[0]) == box and float(r[7]) == l_x:
+            a.append([float(v) for v in r[1:4]])
+            b.append([float(v) for v in r[4:7]])
+    base = rng.random((400, 3)).astype(np.float32)
+    dirs = rng.normal(size=(400, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    for scale in (1.0 - 2.0 ** -22, 1.0, 1.0 + 2.0 ** -22, 0.5, 2.0):
+        far = np.mod(base + (dirs * l_x * scale), box).astype(np.float32)
+        far[far >= np.float32(box)] = 0.0
+        a.extend(base.tolist())
+        b.extend(far.tolist())
+    # wrap: points near 0 against points near the box side on one axis
+    for ax in range(3):
+        p = rng.random((50, 3)).astype(np.float32)
+        q = p.copy()
+        p[:, ax] = rng.random(50).astype(np.float32) * np.float32(l_x / 2)
+        q[:, ax] = np.float32(box) - rng.random(50).astype(np.float32) * np.float32(l_x / 2)
+        q[q >= np.float32(box)] = 0.0
+        a.extend(p.tolist())
+        b.extend(q.tolist())
+    A = np.array(a, dtype=np.float32)
+    B = np.array(b, dtype=np.float32)
+    many = oracle.linked_many(A, B, box, l_x)
+    single = np.array([oracle.linked(A[k], B[k], box, l_x) for k in range(A.shape[0])])
+    assert np.array_equal(many, single)
+    assert many.any() and not many.all()

@@ -14,7 +14,7 @@ def test_candidate_grid_and_options():
     assert len(c) == 3 * 3 * 2
     assert len({json.dumps(x, sort_keys=True) for x in c}) == len(c)
     o = tune.options_from({"occupancy": 0.25, "dense_min": 192, "team_min": 6, "brick_cells": 8})
-    assert (o.occupancy, o.dense_min, o.reserved[0], o.brick_cells) == (0.25, 192, 6, 8)
+    assert (o.occupancy, o.dense_min, o.team_min, o.brick_cells) == (0.25, 192, 6, 8)
     assert o.cells_per_axis == 0 and o.retry_cap == 0           # library defaults kept
     assert tune.options_from(None) is None
 
