@@ -32,10 +32,32 @@ METRIC = "particles grouped/s"
 UNIT = "particles/s"
 
 # Algorithmic bytes per launch of each phase, per particle (p) and per cell
-# (c): what the phase must move at least, not what it happens to move.
+# (c), following the method's byte budget: read the positions (12), write the
+# binned float4 (16) and the forest (4), one read of the binned float4 in the
+# link sweep (16), read the forest at finalisation (4), write ids and sizes
+# (8); 8 per cell for counts and starts.  The whole path: 60 per particle +
+# 8 per cell.
 ALG_BYTES = {
     "bin_count": (12, 0),      # read positions
-    "bin_scatter": (28, 0),    # read positions, write binned float4
+    "bin_scatter": (0, 0),
+    "brick_sort": (20, 8),     # write the binned float4 and parent[s] = s; cell counts + starts
+    "team_self": (0, 0),
+    "big_sort": (0, 0),
+    "dense_self": (0, 0),
+    "dense_pairs": (0, 0),
+    "big_pairs": (0, 0),
+    "link": (16, 0),           # one read of the binned float4
+    "finalize": (4, 0),        # read the forest
+    "outputs": (8, 0),         # write ids and sizes
+    "catalogue": (0, 0),
+    "scan_bricks": (0, 0),
+}
+PATH_BYTES = (60, 8)
+# The bytes each phase of this implementation must move at least, given its
+# two-pass binning and its arrays (reported beside the budget above).
+ALG_BYTES_EXT = {
+    "bin_count": (12, 0),      # read positions
+    "bin_scatter": (28, 0),    # read positions, write brick-order float4
     "brick_sort": (44, 4),     # read float4, write float4 + parent/minorig/cnt, cell starts
     "link": (20, 4),           # read binned float4 + parent once, cell starts once
     "finalize": (8, 0),        # read parent + own index of non-roots
@@ -43,8 +65,6 @@ ALG_BYTES = {
     "catalogue": (4, 0),       # read sizes
     "scan_bricks": (0, 0),
 }
-# The whole path's algorithmic bytes: 60 per particle + 8 per cell.
-PATH_BYTES = (60, 8)
 
 
 def workloads():
@@ -187,6 +207,40 @@ def job_value(n_per_rank: int, world: int, seconds: float) -> float:
 _SAMPLES = {}
 
 
+def host_cpu_info() -> dict:
+    """Core count, CPU model and affinity of this host (for the CPU baselines)."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        info["affinity"] = sorted(os.sched_getaffinity(0))
+        aff = info["affinity"]
+        info["affinity"] = f"{len(aff)} cpus: {aff[0]}-{aff[-1]}" if aff == list(range(aff[0], aff[-1] + 1)) \
+            else ",".join(map(str, aff))
+    except Exception:
+        pass
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    import platform
+    info["cpu_model"] = model or platform.processor() or platform.machine()
+    info["machine"] = platform.machine()
+    return info
+
+
 def cpu_sample(k: int = 8):
     """The oracle on a periodic 1/k^3-volume box of the 1024^3 recipe
     (generated once, then only the oracle is timed)."""
@@ -217,16 +271,21 @@ def run_reference(args):
         c, dt = cpu_sample(args.cpu_k)
         times.append(dt)
     v = c["n"] * len(times) / sum(times)
+    host = host_cpu_info()
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl["name"], "n": wl["n"], "box": wl["box"], "l_x": wl["l_x"],
-                   "min_size": wl["min_size"]},
+        # what each step ran: a bounded sample of the workload (same density,
+        # blob recipe and l_x), named here with its own size
+        "config": {"workload": wl["name"], "sample": c["name"], "n": c["n"], "box": c["box"],
+                   "l_x": c["l_x"], "min_size": c["min_size"],
+                   "sample_of": {"n": wl["n"], "box": wl["box"]}},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{c['name']}: n={c['n']}, box={c['box']}, same density, "
-                                   f"blob recipe and l_x as the full workload"},
+                                   f"blob recipe and l_x as the full workload",
+                         "host": host},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -316,6 +375,8 @@ def run_gpu(args):
     bp, bc = ALG_BYTES[dom]
     alg = bp * n + bc * cells
     achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    ep, ec = ALG_BYTES_EXT.get(dom, (0, 0))
+    alg_ext = ep * n + ec * cells
     traffic = recorded_traffic(dom, wl["name"])
     path_alg = PATH_BYTES[0] * n + PATH_BYTES[1] * cells
     path_gbs = path_alg / (ms_step * 1e-3) / 1e9
@@ -326,27 +387,45 @@ def run_gpu(args):
         ids_h = torch.empty(n, dtype=torch.int32).pin_memory()
         sizes_h = torch.empty(n, dtype=torch.int32).pin_memory()
         cat_h = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
-        fof.fof_run_host(h, pos_pin, ids_h, sizes_h, cat_h, cap, min_size, 1, stream)
+        # every step copies its positions in from pinned host memory and its
+        # ids, sizes and catalogue out; fof_run_host_many overlaps the copies
+        # of one step with the compute of the next
+        fof.fof_run_host_many(h, [pos_pin] * 2, [ids_h] * 2, [sizes_h] * 2, [cat_h] * 2, cap, min_size, 1,
+                              stream)
         torch.cuda.synchronize(dev)
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            _, _, nk_h = fof.fof_run_host(h, pos_pin, ids_h, sizes_h, cat_h, cap, min_size, 1, stream)
+        K = args.steps
+        _, _, nk_h = fof.fof_run_host_many(h, [pos_pin] * K, [ids_h] * K, [sizes_h] * K, [cat_h] * K, cap,
+                                           min_size, 1, stream)
         torch.cuda.synchronize(dev)
         dt = max_over_ranks(time.perf_counter() - t0, world, dev)
-        e2e = {"value": job_value(n * args.steps, world, dt), "unit": UNIT,
+        e2e = {"value": job_value(n * K, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": 12 * n,
-               "d2h_bytes_per_step": 8 * n + 8 * min(nk_h[0], cap) + 64 + 16}
+               "d2h_bytes_per_step": 8 * n + 8 * min(nk_h[-1][0], cap) + 64 + 16,
+               "api": "fof_run_host_many (copies of one step overlap the compute of the next)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         c, dt = cpu_sample(args.cpu_k)
         cpu = {"value": c["n"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{c['name']}: n={c['n']}, box={c['box']}, a periodic box with the "
-                         f"same density, blob recipe and l_x as the full workload"}
+                         f"same density, blob recipe and l_x as the full workload",
+               "host": host_cpu_info()}
 
     fof.fof_destroy(h)
+    # the batched and served forms against the plain per-box loop (one GPU)
+    batched = served = None
+    if world == 1 and wl["name"] == "fof-1024^3-clustered":
+        del pos, ids, sizes, cat, pos_pin
+        if e2e is not None:
+            del ids_h, sizes_h, cat_h
+        torch.cuda.empty_cache()
+        if not args.no_batched:
+            batched = batch_record(args)
+        if not args.no_served:
+            served = served_record(args)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -359,6 +438,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "alg_bytes_per_launch": alg,
+                         "alg_bytes_ext": alg_ext, "frac_ext": alg_ext / (per_launch_ms * 1e-3) / 1e9 / peak,
                          "ms_per_launch": per_launch_ms},
             "path_roofline": {"alg_bytes": path_alg, "achieved": path_gbs, "frac": path_gbs / peak},
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
@@ -367,6 +447,8 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "gen_s": t_gen,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -385,9 +467,10 @@ def _clocks_start():
     return c
 
 
-def run_batch(args):
-    """512 boxes (n log-uniform 16^3..160^3): one batch plan replayed as a CUDA
-    graph vs a loop of per-box plans, both timed with CUDA events."""
+def batch_record(args) -> dict:
+    """The batched form: 512 boxes (n log-uniform 16^3..160^3) in one batch
+    plan replayed as a CUDA graph, against a loop of per-box plans (created
+    before timing), both timed with CUDA events on the same stream."""
     import numpy as np
     import torch
     from paper_2003_11468_gb300 import fof, synth
@@ -399,6 +482,7 @@ def run_batch(args):
     ns = [sp["n"] for sp in specs]
     total = int(sum(ns))
     concat = torch.from_numpy(np.concatenate(poss)).cuda()
+    del poss
     offs = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
     stream = torch.cuda.Stream()
     boxes, lxs = [sp["box"] for sp in specs], [sp["l_x"] for sp in specs]
@@ -411,7 +495,6 @@ def run_batch(args):
             opt, rep = tune.tune(boxes, lxs, ns, concat, repeats=1, min_size=20, stream=stream)
         t_tune = time.perf_counter() - t0
         tuned = {"options": rep["best"], "key": rep["key"], "cached": rep["cached"]}
-    # batched: one plan, one graph
     h = fof.fof_batch_create(boxes, lxs, ns, opt)
     ids_b = torch.empty(total, dtype=torch.int32, device="cuda")
     sizes_b = torch.empty_like(ids_b)
@@ -421,6 +504,7 @@ def run_batch(args):
     for _ in range(args.warmup):
         fof.fof_graph_launch(h, stream)
         fof.fof_result(h, len(specs), stream)
+    launches0 = fof.fof_kernel_launches(h)
     clocks = _clocks_start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -429,7 +513,7 @@ def run_batch(args):
     e1.record(stream)
     code, ng, nk = fof.fof_result(h, len(specs), stream)
     ms_batch = e0.elapsed_time(e1) / args.steps
-    # plain loop: a plan per box (created beforehand), link + groups per box
+    launches = (fof.fof_kernel_launches(h) - launches0) // max(1, args.steps)
     plans = [fof.fof_create_ex(sp["box"], sp["l_x"], sp["n"], opt) for sp in specs]
     ids_p = torch.empty(total, dtype=torch.int32, device="cuda")
     sizes_p = torch.empty_like(ids_p)
@@ -453,79 +537,173 @@ def run_batch(args):
     for hp in plans:
         fof.fof_destroy(hp)
     fof.fof_destroy(h)
-    line = {"metric": "particles grouped/s (batched, one CUDA graph)", "value": total / (ms_batch * 1e-3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic",
-            "config": {"workload": f"batch of {len(specs)} clustered boxes", "particles": total,
-                       "status": code, "tuned": tuned, "tune_s": t_tune},
-            "plain_loop": {"value": total / (ms_plain * 1e-3), "unit": UNIT, "ms_per_step": ms_plain},
-            "speedup_vs_plain": ms_plain / ms_batch, "identical_to_plain": exact,
-            "gpu_launches": None, "clocks": clk, "gen_s": t_gen}
-    print(json.dumps(line), flush=True)
-    return 0
+    del concat, ids_b, sizes_b, cat_b, ids_p, sizes_p, cat_p
+    torch.cuda.empty_cache()
+    return {"metric": "particles grouped/s (batched, one CUDA graph)",
+            "value": total / (ms_batch * 1e-3), "unit": UNIT, "ms_per_step": ms_batch,
+            "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": f"batch of {len(specs)} clustered boxes, n log-uniform 16^3..160^3",
+                       "particles": total, "status": code, "tuned": tuned, "tune_s": t_tune},
+            "plain_loop": {"value": total / (ms_plain * 1e-3), "unit": UNIT, "ms_per_step": ms_plain,
+                           "how": "per-box plans created before timing; fof_link + fof_groups per box"},
+            "speedup_vs_plain": ms_plain / ms_batch, "identical": exact,
+            "gpu_launches_per_step": launches, "clocks": clk, "gen_s": t_gen}
 
 
-def run_served(args):
-    """Poisson requests through the server vs the same requests one by one."""
+def _serve(srv, pool, inputs, jobs, replay: bool):
+    """Submit the jobs (at their arrival times when replay, else at once) and
+    wait for all; returns (seconds, latencies).  Only the latency of each
+    result is kept: results are dropped as soon as they arrive, so the host
+    never holds more than the requests in flight."""
+    done = threading.Semaphore(0)
+    lat, errs = [], []
+    lock = threading.Lock()
+
+    def on_done(f):
+        try:
+            v = f.result().latency_s
+            with lock:
+                lat.append(v)
+        except Exception as e:      # reported after the run
+            with lock:
+                errs.append(e)
+        done.release()
+
+    start = time.perf_counter()
+    for t_arr, k in jobs:
+        if replay:
+            wait = start + t_arr - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+        srv.submit(inputs[k], pool[k]["box"], pool[k]["l_x"], 20).add_done_callback(on_done)
+    for _ in jobs:
+        done.acquire()
+    dt = time.perf_counter() - start
+    if errs:
+        raise errs[0]
+    return dt, lat
+
+
+def served_record(args) -> dict:
+    """The served form against the plain loop, on the same requests.
+
+    Requests: Poisson arrivals (mean 200/s), sizes log-uniform on [1e4, 1e8];
+    each request takes the input of nearest log-size from a pool of distinct
+    inputs (generation is bounded; every input is a real box of that size).
+    Every form copies each request's positions from pinned host memory and
+    its ids and sizes back to host memory.
+      * plain loop: one request at a time, back to back, a plan per distinct
+        size created before timing;
+      * served, all at once: every request submitted at t = 0 -- the server's
+        busy throughput, comparable with the plain loop;
+      * served, Poisson replay: requests submitted at their arrival times --
+        latency from arrival to result (p50/p99); its throughput is bounded
+        by the arrival rate.
+    Throughputs are repeated (args.served_repeats) and given as median,
+    mean and standard deviation."""
     import numpy as np
     import torch
     from paper_2003_11468_gb300 import fof, synth
     from paper_2003_11468_gb300.server import Server
     fof.load()
-    reqs = synth.served_requests(count=args.requests)
-    # a pool of distinct inputs, reused by the requests (bounded generation)
-    pool_n = sorted({int(np.exp(v)) for v in np.linspace(np.log(1e4), np.log(1e8), args.pool)})
+    pool = synth.served_pool(args.pool)
     t0 = time.perf_counter()
-    pool = {}
-    for k, n in enumerate(pool_n):
-        box = 100.0 * (n / 256 ** 3) ** (1.0 / 3.0)
-        pos = synth.clustered_box(n, box, max(1, int(round(20000 * n / 256 ** 3))), seed=5_000_000 + k)
-        pool[n] = (torch.from_numpy(pos).pin_memory(), box, synth.linking_length(n, box))
+    inputs = [torch.from_numpy(synth.make_served(sp)).pin_memory() for sp in pool]
     t_gen = time.perf_counter() - t0
-    keys = np.array(pool_n)
-    jobs = []
-    for r in reqs:
-        n = int(keys[np.argmin(np.abs(np.log(keys) - np.log(r["n"])))])
-        jobs.append((r["t_arrive"], n))
-    total = sum(n for _, n in jobs)
-    # plain: one request at a time, each with its own plan, results to host
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _, n in jobs:
-        pos, box, l_x = pool[n]
-        with fof.FoF(box, l_x, n) as f:
-            ids, sizes, cat, _ = f.run(pos.cuda(non_blocking=True), min_size=20)
-            ids.cpu(), sizes.cpu(), cat.cpu()
-    torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t0
-    # served: Poisson arrivals replayed in real time
+    reqs = synth.served_requests(count=args.requests)
+    logs = np.log(np.array([sp["n"] for sp in pool], dtype=np.float64))
+    jobs = [(r["t_arrive"], int(np.argmin(np.abs(logs - np.log(r["n"]))))) for r in reqs]
+    total = sum(pool[k]["n"] for _, k in jobs)
+
+    def stats(v):
+        return {"median": statistics.median(v), "mean": statistics.fmean(v),
+                "std": statistics.pstdev(v) if len(v) > 1 else 0.0, "runs": v}
+
+    # plain loop: plans and buffers for every distinct size, made before timing
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    plain = []
+    for sp in pool:
+        n = sp["n"]
+        plain.append(dict(h=fof.fof_create(sp["box"], sp["l_x"], n),
+                          pos=torch.empty((n, 3), dtype=torch.float32, device=dev),
+                          ids=torch.empty(n, dtype=torch.int32, device=dev),
+                          sizes=torch.empty(n, dtype=torch.int32, device=dev),
+                          cat=torch.empty((n, 2), dtype=torch.int32, device=dev),
+                          ids_h=torch.empty(n, dtype=torch.int32).pin_memory(),
+                          sizes_h=torch.empty(n, dtype=torch.int32).pin_memory()))
+
+    def plain_pass():
+        for _, k in jobs:
+            P, sp = plain[k], pool[k]
+            with torch.cuda.stream(stream):
+                P["pos"].copy_(inputs[k], non_blocking=True)
+                fof.fof_link(P["h"], P["pos"], stream)
+                _, _, nk = fof.fof_groups(P["h"], P["ids"], P["sizes"], P["cat"], sp["n"], 20, 1, stream)
+                P["ids_h"].copy_(P["ids"], non_blocking=True)
+                P["sizes_h"].copy_(P["sizes"], non_blocking=True)
+                P["cat"][: nk[0]].cpu()
+            stream.synchronize()
+
     clocks = _clocks_start()
-    nmax = max(pool_n)
-    _, bmax, lmax = pool[nmax]
-    with Server(memory_budget=args.budget_gb << 30, slots=args.slots, prealloc=(bmax, lmax, nmax)) as srv:
-        futs = []
-        start = time.perf_counter()
-        for t_arr, n in jobs:
-            wait = start + t_arr - time.perf_counter()
-            if wait > 0:
-                time.sleep(wait)
-            pos, box, l_x = pool[n]
-            futs.append(srv.submit(pos, box, l_x, 20))
-        for f in futs:
-            f.result()
-        t_served = time.perf_counter() - start
-    lat = np.array(srv.latencies)
+    plain_pass()                                   # warm-up
+    t_plain = []
+    for _ in range(args.served_repeats):
+        t0 = time.perf_counter()
+        plain_pass()
+        t_plain.append(total / (time.perf_counter() - t0))
+    big = max(range(len(pool)), key=lambda k: pool[k]["n"])
+    prealloc = (pool[big]["box"], pool[big]["l_x"], pool[big]["n"])
+    at_once, lat, t_poisson, identical = [], None, None, True
+    with Server(memory_budget=args.budget_gb << 30, slots=args.slots, prealloc=prealloc) as srv:
+        # warm-up, and the exactness check against the plain loop's outputs
+        futs = [srv.submit(inputs[k], sp["box"], sp["l_x"], 20) for k, sp in enumerate(pool)]
+        for k, f in enumerate(futs):
+            r = f.result()
+            identical &= bool(np.array_equal(r.ids, plain[k]["ids_h"].numpy())) and \
+                bool(np.array_equal(r.sizes, plain[k]["sizes_h"].numpy()))
+        del futs, r
+        for _ in range(args.served_repeats):
+            dt, _ = _serve(srv, pool, inputs, jobs, replay=False)
+            at_once.append(total / dt)
+        dt, lat = _serve(srv, pool, inputs, jobs, replay=True)
+        t_poisson = total / dt
+        lat = np.array(lat)
+        held_gb = srv.held_bytes() / 2 ** 30
     clk = clocks.stop()
-    line = {"metric": "particles grouped/s (served, Poisson 200/s)", "value": total / t_served, "unit": UNIT,
-            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": t_served * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"{len(jobs)} Poisson requests, n log-uniform 1e4..1e8",
-                       "particles": total, "budget_gb": args.budget_gb, "slots": args.slots},
-            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
-                           "p99": float(np.percentile(lat, 99) * 1e3)},
-            "plain_loop": {"value": total / t_plain, "unit": UNIT, "seconds": t_plain},
-            "clocks": clk, "gen_s": t_gen}
+    for P in plain:
+        fof.fof_destroy(P["h"])
+    del plain, inputs
+    torch.cuda.empty_cache()
+    sa, sp_ = stats(at_once), stats(t_plain)
+    return {"metric": "particles grouped/s (served, continuous batching)",
+            "value": sa["median"], "unit": UNIT,
+            "config": {"workload": f"{len(jobs)} Poisson requests (200/s), n log-uniform 1e4..1e8, "
+                                   f"inputs from a pool of {len(pool)} distinct sizes",
+                       "particles": total, "budget_gb": args.budget_gb, "slots": args.slots,
+                       "repeats": args.served_repeats},
+            "served_all_at_once": sa,
+            "plain_loop": dict(sp_, how="one request at a time; plans and buffers made before timing; "
+                                        "H2D of positions and D2H of ids/sizes/catalogue per request"),
+            "speedup_vs_plain": sa["median"] / sp_["median"],
+            "poisson_replay": {"value": t_poisson, "unit": UNIT,
+                               "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                                              "p99": float(np.percentile(lat, 99) * 1e3)}},
+            "identical": identical, "server_held_gb": held_gb, "clocks": clk, "gen_s": t_gen}
+
+
+def run_batch(args):
+    line = batch_record(args)
+    line.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                 "dtype": "f32+f64", "data": "synthetic"})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    line = served_record(args)
+    line.update({"n_gpus": 1, "steps": args.served_repeats, "warmup": 1, "higher_is_better": True,
+                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -539,7 +717,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batch workload: library default options")
     ap.add_argument("--workload", default="1024", choices=["1024", "1024s", "256", "32k", "batch", "served"])
     ap.add_argument("--boxes", type=int, default=512, help="batch workload: number of boxes")
-    ap.add_argument("--requests", type=int, default=400, help="served workload: requests")
+    ap.add_argument("--requests", type=int, default=2000, help="served workload: requests")
+    ap.add_argument("--served-repeats", type=int, default=3, help="served workload: timed repeats")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-record")
+    ap.add_argument("--no-served", action="store_true", help="skip the served sub-record")
     ap.add_argument("--pool", type=int, default=24, help="served workload: distinct inputs")
     ap.add_argument("--slots", type=int, default=3)
     ap.add_argument("--budget-gb", type=int, default=120)

@@ -187,6 +187,22 @@ size_t fof_batch_workspace_bytes(int32_t nbox, const double *box, const double *
  * handle, NULL pos_dev with n > 0), FOF_ERR_CUDA. */
 int fof_link(fof_handle h, const float *pos_dev, void *stream);
 
+/* fof_link for particles that moved since the last fof_link or fof_relink
+ * of this plan (the paper runs the group finder on-the-fly at fixed
+ * intervals of a simulation, Sec. 1, and suggests re-using the existing
+ * data structures): same arguments, results and errors as fof_link, with
+ * pos_dev holding the SAME particles (same count and order) at new
+ * positions.  The previous binned order is kept where it still holds:
+ *   path 0: no particle left its cell -- positions are updated in place and
+ *           the cells, cell starts and cell lists are re-used;
+ *   path 1: particles changed cells but none left its brick (16^3 cells)
+ *           -- only the per-brick cell sort runs again;
+ *   path 2: otherwise (or with no previous binning) -- fof_link.
+ * *path_out (may be NULL) receives the path taken.  Unlike fof_link it
+ * waits once for `stream` (to read which path applies), so it cannot be
+ * captured in a CUDA graph. */
+int fof_relink(fof_handle h, const float *pos_dev, int32_t *path_out, void *stream);
+
 /* Enqueue finalisation and outputs of the last fof_link, then wait for the
  * stream and report.  ids_dev and sizes_dev hold sum(n) int32 each;
  * catalogue_dev holds cat_capacity fof_group entries; NULL (with
@@ -221,6 +237,22 @@ int fof_result(fof_handle h, int64_t *n_groups_out, int64_t *n_cat_out, void *st
 int fof_run_host(fof_handle h, const float *pos_host, int32_t *ids_host, int32_t *sizes_host,
                  fof_group *catalogue_host, int64_t cat_capacity, int32_t min_size,
                  int64_t *n_groups_out, int64_t *n_cat_out, void *stream);
+
+/* fof_run_host over `nsteps` inputs (for example the snapshots of a
+ * simulation, each with this plan's particle count), pipelined: the
+ * positions of step k+1 are copied in, on a copy stream, while step k
+ * runs on `stream`, and the results of step k are copied out, on a second
+ * copy stream, while step k+1 runs.  pos_host[k], ids_host[k],
+ * sizes_host[k] and catalogue_host[k] are step k's host buffers (pinned
+ * memory overlaps best); n_groups_out / n_cat_out (may be NULL) receive
+ * nsteps x nbox counts, step-major.  Returns after every result is in host
+ * memory.  Two device staging sets, the copy streams and their events are
+ * made on the first call and kept by the handle.  Same errors as
+ * fof_run_host; FOF_ERR_CAPACITY if any step's catalogue was cut. */
+int fof_run_host_many(fof_handle h, int32_t nsteps, const float *const *pos_host,
+                      int32_t *const *ids_host, int32_t *const *sizes_host,
+                      fof_group *const *catalogue_host, int64_t cat_capacity, int32_t min_size,
+                      int64_t *n_groups_out, int64_t *n_cat_out, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* CUDA graph of the whole pipeline                                        */
@@ -278,6 +310,31 @@ int64_t fof_kernel_launches(fof_handle h);
 
 void fof_destroy(fof_handle h);
 const char *fof_strerror(int code);
+
+/* ---------------------------------------------------------------------- */
+/* groups spanning several domains (one GPU per domain)                    */
+/* ---------------------------------------------------------------------- */
+
+/* The merge step of the distributed group finder (paper Sec. 3.3, Fig.
+ * "Distributed Union-Find", steps 3-4; hash table of group ids, Sec. 3.4.1).
+ * Every domain first finds the groups of its own particles plus a ghost
+ * layer of width l_x, labels each local group with a globally unique id,
+ * and lists links (a[k], b[k]) between ids that name the same group (for
+ * example a ghost particle's id and the id of the local group holding it).
+ * The links of all domains are gathered (all-gather), and this function runs
+ * the union-find over the whole list, following indirect links through
+ * third domains.  Sets are joined by size (Sec. 3.3); `weights` (may be
+ * NULL with nweights 0) give the size of the ids in weight_ids, other ids
+ * weigh 1 per first appearance.
+ * For each query[k], label_out[k] receives the SMALLEST id of its merged
+ * set (the id itself when it appears in no link or weight), and
+ * weight_out[k] (may be NULL) the set's total weight (0 for such ids).
+ * Host pointers, int64; nothing is kept between calls.  Host code only:
+ * needs no GPU.  Errors: FOF_ERR_ARG (negative counts, NULL arrays with
+ * non-zero counts), FOF_ERR_OOM. */
+int fof_merge_links(int64_t npairs, const int64_t *a, const int64_t *b, int64_t nweights,
+                    const int64_t *weight_ids, const int64_t *weights, int64_t nq,
+                    const int64_t *query, int64_t *label_out, int64_t *weight_out);
 
 /* ---------------------------------------------------------------------- */
 /* allocation-free single-box run                                          */

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfof_gb300.so")
-SOURCES = ["fof_bin.cu", "fof_dense.cu", "fof_link.cu", "fof_out.cu", "fof_plan.cu"]
+SOURCES = ["fof_big.cu", "fof_bin.cu", "fof_dense.cu", "fof_link.cu", "fof_merge.cu", "fof_out.cu", "fof_plan.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

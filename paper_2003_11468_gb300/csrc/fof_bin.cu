@@ -207,11 +207,13 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
                                                              int* __restrict__ n_dense,
                                                              int dense_min,
                                                              int64_t* __restrict__ team_list,
-                                                             int* __restrict__ n_team)
+                                                             int* __restrict__ n_team,
+                                                             int64_t* __restrict__ big_list,
+                                                             int* __restrict__ n_big)
 {
     __shared__ int hist[kMaxR3];
     __shared__ int sw[32];
-    __shared__ int list_base[2];
+    __shared__ int list_base[3];
     for (int64_t gb = blockIdx.x; gb < g.total_bricks; gb += gridDim.x) {
         const int bi = box_of(g.box_brick0, g.nbox, gb);
         const BoxDev& b = g.boxes[bi];
@@ -235,35 +237,42 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
         int ex = block_exclusive_scan(run, sw, total);
         const int ex0 = ex;
         const int64_t cbase = b.cell0 + (gb - b.brick0) * (int64_t)r3;
-        int nd = 0, nt = 0;                     // this thread's dense and team cells
+        int nd = 0, nt = 0, nbg = 0;            // this thread's dense, team and big cells
         for (int c = c0; c < c0 + per && c < r3; ++c) {
             const int h = hist[c];
             cell_start[cbase + c] = s0 + ex;
             ex += h;
-            if (is_sub(h, b, dense_min))
+            if (is_big(h, b))
+                ++nbg;
+            else if (is_sub(h, b, dense_min))
                 ++nd;
             else if (h >= b.team_min && h <= kTeamSelfMax)
                 ++nt;
         }
         // list slots: one reservation per brick (a shared counter per cell
         // would serialise millions of atomics on one address)
-        int nd_tot, nt_tot;
+        int nd_tot, nt_tot, nb_tot;
         int od = block_exclusive_scan(nd, sw, nd_tot);
         int ot = block_exclusive_scan(nt, sw, nt_tot);
+        int obg = block_exclusive_scan(nbg, sw, nb_tot);
         if (threadIdx.x == 0) {
             list_base[0] = nd_tot ? atomicAdd(n_dense, nd_tot) : 0;
             list_base[1] = nt_tot ? atomicAdd(n_team, nt_tot) : 0;
+            list_base[2] = nb_tot ? atomicAdd(n_big, nb_tot) : 0;
         }
         __syncthreads();
         od += list_base[0];
         ot += list_base[1];
+        obg += list_base[2];
         ex = ex0;
         for (int c = c0; c < c0 + per && c < r3; ++c) {
             const int h = hist[c];
             const int start = s0 + ex;
             hist[c] = ex;                       // becomes the cursor
             ex += h;
-            if (is_sub(h, b, dense_min))
+            if (is_big(h, b))
+                big_list[obg++] = cbase + c;
+            else if (is_sub(h, b, dense_min))
                 dense_list[od++] = cbase + c;
             else if (h >= b.team_min && h <= kTeamSelfMax)
                 team_list[ot++] = ((int64_t)h << 32) | (uint32_t)start;
@@ -287,6 +296,61 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
         if (gb == g.total_bricks - 1 && threadIdx.x == 0)
             cell_start[g.total_cells] = (int)g.total_n;
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------
+// incremental re-binning (the group finder run again on moved particles)
+// ------------------------------------------------------------------------
+
+// For every binned slot s of the previous run: the particle's new position
+// (pos[p0 + local index]) replaces its old one in sorted[s] and tmp[s], and
+// flags record whether it left its cell (bit 0) or its brick (bit 1).  When
+// no particle left its brick, the slots are still grouped by brick, so
+// tmp[] is a valid brick-order array for k_brick_sort; when no particle left
+// its cell, sorted[] and the cell starts and lists are valid as they are.
+__global__ void __launch_bounds__(256) k_relink_check(const float* __restrict__ pos, Geometry g,
+                                                      float4* __restrict__ sorted, float4* __restrict__ tmp,
+                                                      int* __restrict__ flags, int* __restrict__ err)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int f = 0, bad = 0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < g.total_n; s += stride) {
+        const BoxDev& b = g.boxes[box_of(g.box_p0, g.nbox, s)];
+        const float4 old = sorted[s];
+        const int o = __float_as_int(old.w);
+        const int64_t i = b.p0 + o;
+        float4 rec;
+        bool ok;
+        const int64_t nb = brick_of(pos, i, b, rec, ok);
+        bad |= !ok;
+        const int ox = cell_coord(old.x, b), oy = cell_coord(old.y, b), oz = cell_coord(old.z, b);
+        const int nx = cell_coord(rec.x, b), ny = cell_coord(rec.y, b), nz = cell_coord(rec.z, b);
+        if (nx != ox || ny != oy || nz != oz)
+            f |= 1;
+        if (nb != b.brick0 + brick_local(b, ox, oy, oz))
+            f |= 2;
+        sorted[s] = rec;
+        tmp[s] = rec;
+    }
+    f = __reduce_or_sync(kFull, f);
+    if ((threadIdx.x & 31) == 0 && f)
+        atomicOr(flags, f);
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+        atomicOr(err, kErrRange);
+}
+
+// Forest and label initialisation of the binned slots (what k_brick_sort
+// does while it sorts): parent[s] = s, cnt[s] = 1, minorig[s] = local index.
+__global__ void __launch_bounds__(256) k_forest_init(int64_t total, const float4* __restrict__ sorted,
+                                                     int* __restrict__ parent, int* __restrict__ minorig,
+                                                     int* __restrict__ cnt)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total; s += stride) {
+        parent[s] = (int)s;
+        cnt[s] = 1;
+        minorig[s] = __float_as_int(sorted[s].w);
     }
 }
 
@@ -347,7 +411,27 @@ cudaError_t launch_brick_sort(const Geometry& g, const Work& w, int dense_min, c
     k_brick_sort<<<(unsigned)blocks, kSortThreads, 0, s>>>(g, w.tmp, w.bstart, w.sorted, w.parent,
                                                          w.minorig, w.cnt, w.cell_start,
                                                          &w.status->err, w.dense_list, w.n_dense,
-                                                         dense_min, w.team_list, w.n_team);
+                                                         dense_min, w.team_list, w.n_team, w.big_list,
+                                                         w.n_big);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relink_check(const float* pos, const Geometry& g, const Work& w, int* flags,
+                                cudaStream_t s)
+{
+    if (g.total_n == 0)
+        return cudaSuccess;
+    k_relink_check<<<grid_for(g.total_n, 256, 8), 256, 0, s>>>(pos, g, w.sorted, w.tmp, flags,
+                                                             &w.status->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forest_init(const Geometry& g, const Work& w, cudaStream_t s)
+{
+    if (g.total_n == 0)
+        return cudaSuccess;
+    k_forest_init<<<grid_for(g.total_n, 256, 8), 256, 0, s>>>(g.total_n, w.sorted, w.parent, w.minorig,
+                                                             w.cnt);
     return cudaGetLastError();
 }
 

@@ -187,9 +187,10 @@ __device__ __forceinline__ int build_cell(const DenseSmem& S, const float4* __re
 // sub-cell a (possibly stale: equal roots prove one group, different ones
 // only mean "test").  single: the cell is one group, so the first link is
 // enough.  Returns pj's root after the unions it made.
+template <bool kVar>
 __device__ __forceinline__ int link_window(const DenseSmem& S, int* parent, const BoxDev& b,
                                            float4 pj, int rj, int rx, int ry, int rz, bool single,
-                                           int cap, int* err, bool& linked_any)
+                                           const UfArgs& uf, bool& linked_any)
 {
     const int q = b.q;
     const int x0 = max(rx - 2, 0), x1 = min(rx + 2, q - 1);
@@ -218,7 +219,7 @@ __device__ __forceinline__ int link_window(const DenseSmem& S, int* parent, cons
                     continue;
                 for (int t = beg; t < end; ++t) {
                     if (linked_ool(pj, S.P[S.order[t]], b)) {
-                        rj = uf_union(parent, rj, S.groot[a], cap, err);
+                        rj = uunion<kVar>(parent, rj, S.groot[a], uf);
                         linked_any = true;
                         if (single)
                             return rj;
@@ -278,12 +279,13 @@ __device__ __forceinline__ int neighbour_of(const DenseSmem& S, int t)
     return lo;
 }
 
+template <bool kVar>
 __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_self(Geometry g, Work w, int dense_min,
-                                                              int cap)
+                                                              UfArgs uf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DenseSmem S = carve(smem_raw);
-    int* err = &w.status->err;
+    int* err = uf.err;
     const int n_dense = *w.n_dense;
     for (int it = blockIdx.x; it < n_dense; it += gridDim.x) {
         const int64_t key = w.dense_list[it];
@@ -421,14 +423,14 @@ __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_self(Geometry g, Wor
             int rx, ry, rz;
             if (!rel_fine(pj, b, ox, oy, oz, rx, ry, rz))
                 continue;
-            int rj = uf_find(w.parent, j, err);
+            int rj = ufind<kVar>(w.parent, j, uf);
             if (single >= 0) {
-                ru = uf_find(w.parent, ru, err);
+                ru = ufind<kVar>(w.parent, ru, uf);
                 if (rj == ru)
                     continue;
             }
             bool any = false;
-            int r = link_window(S, w.parent, b, pj, rj, rx, ry, rz, single >= 0, cap, err, any);
+            int r = link_window<kVar>(S, w.parent, b, pj, rj, rx, ry, rz, single >= 0, uf, any);
             if (any && single >= 0)
                 ru = r;
         }
@@ -436,12 +438,13 @@ __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_self(Geometry g, Wor
     }
 }
 
+template <bool kVar>
 __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_pairs(Geometry g, Work w, int dense_min,
-                                                               int cap)
+                                                               UfArgs uf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DenseSmem S = carve(smem_raw);
-    int* err = &w.status->err;
+    int* err = uf.err;
     const int n_dense = *w.n_dense;
     for (int it = blockIdx.x; it < n_dense; it += gridDim.x) {
         const int64_t key = w.dense_list[it];
@@ -463,10 +466,10 @@ __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_pairs(Geometry g, Wo
                 int64_t nk = nbr_cell(b, cx, cy, cz, dx, dy, dz);
                 int j0 = w.cell_start[nk], j1 = w.cell_start[nk + 1];
                 int both = 0;
-                if (is_sub(j1 - j0, b, dense_min)) {
+                if (is_sub(j1 - j0, b, dense_min) && !is_big(j1 - j0, b)) {
                     int ub = w.dense_root[j0 / dense_min];
                     both = ua >= 0 && ub >= 0;
-                    cnt = (both && uf_find(w.parent, ua, err) == uf_find(w.parent, ub, err)) ? 0 : j1 - j0;
+                    cnt = (both && ufind<kVar>(w.parent, ua, uf) == ufind<kVar>(w.parent, ub, uf)) ? 0 : j1 - j0;
                 }
                 S.nbj0[k] = j0;
                 S.nbflag[k] = both;
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_pairs(Geometry g, Wo
         build_cell(S, w.sorted, c0, m, b, ox, oy, oz, err);
         for (int a = threadIdx.x; a < q * q * q; a += blockDim.x)
             if (S.sstart[a + 1] > S.sstart[a])
-                S.groot[a] = uf_find(w.parent, c0 + S.order[S.sstart[a]], err);
+                S.groot[a] = ufind<kVar>(w.parent, c0 + S.order[S.sstart[a]], uf);
         __syncthreads();
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
             int lo = 0, hi = 12;
@@ -505,9 +508,9 @@ __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_pairs(Geometry g, Wo
             int rx, ry, rz;
             if (!rel_fine(pj, b, ox, oy, oz, rx, ry, rz))
                 continue;
-            int rj = uf_find(w.parent, j, err);
+            int rj = ufind<kVar>(w.parent, j, uf);
             bool any = false;
-            link_window(S, w.parent, b, pj, rj, rx, ry, rz, single, cap, err, any);
+            link_window<kVar>(S, w.parent, b, pj, rj, rx, ry, rz, single, uf, any);
             if (any && single)
                 S.nbdone[k] = 1;
         }
@@ -522,7 +525,17 @@ size_t dense_smem()
     return dense_smem_bytes();
 }
 
-cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, int retry_cap, bool pairs,
+template <bool kVar>
+cudaError_t configure_dense()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_dense_self<kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dense_smem_bytes());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_dense_pairs<kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dense_smem_bytes());
+}
+
+cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, const UfArgs& uf, bool pairs,
                          cudaStream_t s)
 {
     // the shared-memory opt-in is per device; setting it again is harmless
@@ -531,19 +544,25 @@ cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, int re
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(k_dense_self, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dense_smem_bytes());
+        e = configure_dense<false>();
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_dense_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dense_smem_bytes());
+        e = configure_dense<true>();
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    int blocks = sm_count() * 2;
-    if (pairs)
-        k_dense_pairs<<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, retry_cap);
-    else
-        k_dense_self<<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, retry_cap);
+    const int blocks = sm_count() * 2;
+    const bool var = uf.find != 0 || uf.link != 0;
+    if (pairs) {
+        if (var)
+            k_dense_pairs<true><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);
+        else
+            k_dense_pairs<false><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);
+    } else {
+        if (var)
+            k_dense_self<true><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);
+        else
+            k_dense_self<false><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);
+    }
     return cudaGetLastError();
 }
 

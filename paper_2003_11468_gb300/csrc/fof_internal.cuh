@@ -52,9 +52,12 @@ struct BoxDev {
                       // bounding box beyond which no partner lies
 };
 
-// A cell is "subdivided" (linked by the dense kernels) when its box splits
-// cells (q > 1) and it holds between dense_min and kDenseMax particles.
-constexpr int kDenseMax = 3072;   // particles of a subdivided cell (shared memory)
+// A cell is "subdivided" (linked by the sub-cell kernels, never pair by
+// pair) when its box splits cells (q > 1) and it holds at least dense_min
+// particles: up to kDenseMax particles it is a dense cell, staged in shared
+// memory (fof_dense.cu); above, a big cell, sorted by sub-cell in global
+// memory (fof_big.cu).
+constexpr int kDenseMax = 3072;   // particles of a dense cell (shared memory)
 // Largest team cell whose own pairs one warp links in shared memory
 // (k_team_self); larger unsplit cells link their own pairs in k_link.
 constexpr int kTeamSelfMax = 256;
@@ -111,7 +114,12 @@ __device__ __forceinline__ int cell_coord(float x, const BoxDev& b)
 
 __device__ __forceinline__ bool is_sub(int m, const BoxDev& b, int dense_min)
 {
-    return b.q > 1 && m >= dense_min && m <= kDenseMax;
+    return b.q > 1 && m >= dense_min;
+}
+
+__device__ __forceinline__ bool is_big(int m, const BoxDev& b)
+{
+    return b.q > 1 && m > kDenseMax;
 }
 
 __device__ __forceinline__ uint32_t spread3(uint32_t v)   // 5 bits -> every 3rd bit
@@ -290,6 +298,126 @@ __device__ __forceinline__ int uf_union(int* parent, int a, int b, int cap, int*
 }
 
 // ------------------------------------------------------------------------
+// union-find variants (measured against the default; same partition)
+// ------------------------------------------------------------------------
+
+// Arguments of every union-find call of a kernel.  `find` and `link` select
+// the variants of fof.h (FOF_FIND_*, FOF_LINK_*); they are read only by the
+// kernels' variant instantiation (kVar = true), so the default path carries
+// no runtime switch.
+struct UfArgs {
+    int cap;     // CAS attempts per union
+    int* err;    // status word
+    int find;    // 0 halving on paths of depth >= 2, 1 halving at every depth,
+                 // 2 full compression, 3 none
+    int link;    // 0 hook the larger root onto the smaller, 1 randomised
+};
+
+// Random priority of a root for randomised linking: the 32-bit finaliser of
+// MurmurHash3, a bijection, so distinct roots never tie.
+__device__ __forceinline__ uint32_t uf_priority(int x)
+{
+    uint32_t h = (uint32_t)x;
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Find under the selected compression.  Every value parent[x] ever holds is
+// an ancestor of x in every variant, so racing writes stay harmless.  The
+// ordering check (a parent never exceeds its child) holds only when roots
+// hook onto smaller roots.
+__device__ __forceinline__ int uf_find_var(int* parent, int x, const UfArgs& u)
+{
+    const bool ordered = u.link == 0;
+    if (u.find == 2) {                              // full compression
+        // The first walk records the nodes it passes; every one of them has
+        // the root r found as an ancestor for good (trees only merge), so
+        // pointing them at r is safe.  Walking the path a second time would
+        // not be: other threads may have re-pointed it past r, and writing r
+        // into an ancestor of r would close a cycle.
+        constexpr int kPath = 16;
+        int path[kPath];
+        int len = 0;
+        int r = x;
+        int p = ld_relaxed(parent + r);
+        for (int step = 0; p != r; ++step) {
+            if (step >= kFindCap || (ordered && p > r)) {
+                atomicOr(u.err, kErrInternal);
+                return p;
+            }
+            if (len < kPath)
+                path[len++] = r;
+            r = p;
+            p = ld_relaxed(parent + r);
+        }
+        for (int k = 0; k + 1 < len; ++k)            // the last one already points at r
+            st_relaxed(parent + path[k], r);
+        return r;
+    }
+    int p = ld_relaxed(parent + x);
+    for (int step = 0; p != x; ++step) {
+        const int gp = ld_relaxed(parent + p);
+        if (step >= kFindCap || (ordered && gp > p)) {
+            atomicOr(u.err, kErrInternal);
+            return p;
+        }
+        if (gp == p) {
+            if (u.find == 1)
+                st_relaxed(parent + x, gp);         // the depth-1 rewrite (same value)
+            return p;
+        }
+        if (u.find == 3) {                          // no compression: plain walk
+            x = p;
+            p = gp;
+            continue;
+        }
+        st_relaxed(parent + x, gp);
+        x = gp;
+        p = ld_relaxed(parent + x);
+    }
+    return x;
+}
+
+__device__ __forceinline__ int uf_union_var(int* parent, int a, int b, const UfArgs& u)
+{
+    for (int it = 0; it < u.cap; ++it) {
+        a = uf_find_var(parent, a, u);
+        b = uf_find_var(parent, b, u);
+        if (a == b)
+            return a;
+        int hi, lo;                                 // hi is hooked onto lo
+        if (u.link == 1) {
+            const bool a_wins = uf_priority(a) > uf_priority(b);
+            lo = a_wins ? a : b;
+            hi = a_wins ? b : a;
+        } else {
+            hi = a > b ? a : b;
+            lo = a > b ? b : a;
+        }
+        if (atomicCAS(parent + hi, hi, lo) == hi)
+            return lo;
+    }
+    atomicOr(u.err, kErrTimeout);
+    return a < b ? a : b;
+}
+
+template <bool kVar>
+__device__ __forceinline__ int ufind(int* parent, int x, const UfArgs& u)
+{
+    return kVar ? uf_find_var(parent, x, u) : uf_find(parent, x, u.err);
+}
+
+template <bool kVar>
+__device__ __forceinline__ int uunion(int* parent, int a, int b, const UfArgs& u)
+{
+    return kVar ? uf_union_var(parent, a, b, u) : uf_union(parent, a, b, u.cap, u.err);
+}
+
+// ------------------------------------------------------------------------
 // kernel launchers (one per phase); each returns cudaGetLastError()
 // ------------------------------------------------------------------------
 
@@ -326,6 +454,8 @@ struct Work {
     int* n_dense;        // number of entries in dense_list
     int* dense_root;     // [total_n / dense_min + 1] by first slot / dense_min:
                          // root of a subdivided cell that is one group, else -1
+    int64_t* big_list;   // [big_cap] cell keys of the big cells (subdivided, > kDenseMax)
+    int* n_big;          // number of entries in big_list
     int64_t* team_list;  // [team_cap] team cells (team_min..kTeamSelfMax particles, not
                          // subdivided): size << 32 | first slot
     int* n_team;         // number of entries in team_list
@@ -343,13 +473,23 @@ cudaError_t launch_scan(const int* in, int* out, int64_t len, int* tmp, int64_t 
 int64_t scan_tmp_elems(int64_t len);
 cudaError_t launch_bin_scatter(const float* pos, const Geometry& g, const Work& w, cudaStream_t s);
 cudaError_t launch_brick_sort(const Geometry& g, const Work& w, int dense_min, cudaStream_t s);
-cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, int retry_cap, bool pairs,
+// incremental re-binning: flags |= 1 if a particle left its cell, 2 if it left its brick
+cudaError_t launch_relink_check(const float* pos, const Geometry& g, const Work& w, int* flags,
+                                cudaStream_t s);
+cudaError_t launch_forest_init(const Geometry& g, const Work& w, cudaStream_t s);
+cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, const UfArgs& uf, bool pairs,
                          cudaStream_t s);
 size_t dense_smem();
-cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, int retry_cap,
+cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, const UfArgs& uf,
                         cudaStream_t s);
 cudaError_t launch_team_self(const Geometry& g, const Work& w, cudaStream_t s);
-cudaError_t launch_finalize(const Geometry& g, const Work& w, cudaStream_t s);
+// big cells: sort by sub-cell + own pairs (before the dense kernels), then
+// their pairs with every neighbour (after them)
+cudaError_t launch_big(const Geometry& g, const Work& w, int dense_min, const UfArgs& uf, bool pairs,
+                       cudaStream_t s);
+// size_count: 0 warp-aggregated atomics, 1 per-block shared-memory hash table
+cudaError_t launch_finalize(const Geometry& g, const Work& w, const UfArgs& uf, int size_count,
+                            cudaStream_t s);
 cudaError_t launch_outputs(const Geometry& g, const Work& w, int32_t* ids, int32_t* sizes,
                            int32_t min_size, cudaStream_t s);
 cudaError_t launch_catalogue(const Geometry& g, const Work& w, const int32_t* sizes,

@@ -173,10 +173,11 @@ constexpr int kOwnCell = 13;     // stream index of a team's own cell (cells abo
 //     whose roots already agree; linked pairs set bits in the member's link
 //     mask;
 //   * each member then merges with the distinct candidate roots it links to.
+template <bool kVar>
 __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent,
                                           const float4* __restrict__ sorted, const BoxDev& b, int lane,
                                           int lo, int m, int first, const Cell& tc, int j0k, int cntk,
-                                          const TeamBox& tb, bool filter, int cap, int* err)
+                                          const TeamBox& tb, bool filter, const UfArgs& uf)
 {
     const int start_k = warp_incl(cntk, lane) - cntk;
     const int total = __shfl_sync(kFull, start_k + cntk, 31);
@@ -210,7 +211,7 @@ __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent
         const unsigned cand = __ballot_sync(kFull, jv);
         if (!cand)
             continue;
-        const int rj = jv ? uf_find(parent, j, err) : -1;
+        const int rj = jv ? ufind<kVar>(parent, j, uf) : -1;
         const int ref = S.mroot[0];
         const int mr = lane < m ? S.mroot[lane] : ref;
         if (__all_sync(kFull, mr == ref && (!jv || rj == ref)))
@@ -254,7 +255,7 @@ __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent
                     links &= links - 1u;
                     const int rt = S.croot[u];
                     if (rt != ri && rt != last) {
-                        ri = uf_union(parent, ri, rt, cap, err);
+                        ri = uunion<kVar>(parent, ri, rt, uf);
                         last = rt;
                     }
                 }
@@ -266,9 +267,10 @@ __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent
     }
 }
 
+template <bool kVar>
 __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4* __restrict__ sorted,
                                                        const int* __restrict__ cell_start, int* parent,
-                                                       int dense_min, int cap, int* err)
+                                                       int dense_min, UfArgs uf)
 {
     __shared__ TeamStage stage[kLinkWarps];
     const int lane = threadIdx.x & 31;
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
             const unsigned team_reach = __reduce_or_sync(kFull, reach);
             if (mine) {
                 S.mpos[lane - lead] = make_float4(p.x, p.y, p.z, __int_as_float((int)reach));
-                S.mroot[lane - lead] = uf_find(parent, (int)s, err);
+                S.mroot[lane - lead] = ufind<kVar>(parent, (int)s, uf);
             }
             const int first = (int)__shfl_sync(kFull, s, lead);
             const int cell_end = __shfl_sync(kFull, c1, lead);
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                 cntk = lo;
             }
             __syncwarp();
-            team_cell(S, parent, sorted, b, lane, lead, m, first, tc, j0k, cntk, tbx, b.nc >= 3, cap, err);
+            team_cell<kVar>(S, parent, sorted, b, lane, lead, m, first, tc, j0k, cntk, tbx, b.nc >= 3, uf);
         }
 
         // ---- sparse particles: their (particle, cell) items, then their
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                 if (uv) {
                     const BoxDev& b = g.boxes[pbi];
                     if (linked(po, sorted[jj], b))
-                        uf_union(parent, (int)(base + oo), jj, cap, err);
+                        uunion<kVar>(parent, (int)(base + oo), jj, uf);
                 }
             }
         }
@@ -777,16 +779,18 @@ cudaError_t launch_team_self(const Geometry& g, const Work& w, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, int retry_cap, cudaStream_t s)
+cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, const UfArgs& uf, cudaStream_t s)
 {
     if (g.total_n == 0)
         return cudaSuccess;
     int64_t warps = (g.total_n + kWarp - 1) / kWarp;
-    int64_t blocks = (warps * kWarp + 255) / 256;
+    int64_t blocks = (warps * kWarp + kLinkThreads - 1) / kLinkThreads;
     int64_t cap = (int64_t)sm_count() * 8;
     if (blocks > cap) blocks = cap;
-    k_link<<<(unsigned)blocks, 256, 0, s>>>(g, w.sorted, w.cell_start, w.parent, dense_min, retry_cap,
-                                            &w.status->err);
+    if (uf.find != 0 || uf.link != 0)
+        k_link<true><<<(unsigned)blocks, kLinkThreads, 0, s>>>(g, w.sorted, w.cell_start, w.parent, dense_min, uf);
+    else
+        k_link<false><<<(unsigned)blocks, kLinkThreads, 0, s>>>(g, w.sorted, w.cell_start, w.parent, dense_min, uf);
     return cudaGetLastError();
 }
 

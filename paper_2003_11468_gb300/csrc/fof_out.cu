@@ -18,9 +18,31 @@ namespace fofgpu {
 
 namespace {
 
+// Root of slot s by a plain walk, then parent[s] = root.  `ordered`: every
+// parent is at most its child (hooks onto the smaller root), checked.
+__device__ __forceinline__ int final_root(int* __restrict__ parent, int s, bool ordered, int* err)
+{
+    const int p = parent[s];
+    if (p == s)
+        return s;
+    int x = p;
+    int q = parent[x];
+    for (int step = 0; q != x; ++step) {
+        if ((ordered && q > x) || step >= kFindCap) {   // corrupted forest: report
+            atomicOr(err, kErrInternal);
+            break;
+        }
+        x = q;
+        q = parent[x];
+    }
+    if (p != x)
+        parent[s] = x;
+    return x;
+}
+
 __global__ void __launch_bounds__(256) k_finalize(int64_t total, int* __restrict__ parent,
                                                   int* __restrict__ minorig, int* __restrict__ cnt,
-                                                  int* __restrict__ err)
+                                                  int* __restrict__ err, bool ordered)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
@@ -29,23 +51,7 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t total, int* __restrict
         unsigned active = __ballot_sync(kFull, valid);
         if (!valid)
             continue;
-        int p = parent[s];
-        int root = (int)s;
-        if (p != (int)s) {
-            int x = p;
-            int q = parent[x];
-            for (int step = 0; q != x; ++step) {
-                if (q > x || step >= kFindCap) {   // corrupted forest: report
-                    atomicOr(err, kErrInternal);
-                    break;
-                }
-                x = q;
-                q = parent[x];
-            }
-            root = x;
-            if (p != root)
-                parent[s] = root;
-        }
+        const int root = final_root(parent, (int)s, ordered, err);
         bool nonroot = root != (int)s;
         unsigned nr = __ballot_sync(active, nonroot);
         if (!nonroot)
@@ -57,6 +63,87 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t total, int* __restrict
             atomicAdd(cnt + root, __popc(peers));
             atomicMin(minorig + root, (int)mn);
         }
+    }
+}
+
+// The same finalisation with the paper's hash-table size count (Sec. 3.4.1):
+// each block gathers (root, count, smallest index) of the non-roots of
+// kHashBatch consecutive slot tiles in an open-addressing table in shared
+// memory, then adds each entry to the root with one atomic per entry (roots
+// are not entered: their own contribution is the initial size 1, Sec.
+// 3.4.2).  A slot whose probe sequence finds no room adds itself directly.
+constexpr int kHashSlots = 4096;     // power of two
+constexpr int kHashBatch = 8;        // tiles of 256 slots per flush: <= 2048 keys, load <= 1/2
+constexpr int kHashProbes = 16;
+
+__global__ void __launch_bounds__(256) k_finalize_hash(int64_t total, int* __restrict__ parent,
+                                                       int* __restrict__ minorig, int* __restrict__ cnt,
+                                                       int* __restrict__ err, bool ordered)
+{
+    __shared__ int hkey[kHashSlots];
+    __shared__ int hcnt[kHashSlots];
+    __shared__ int hmin[kHashSlots];
+    for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x)
+        hkey[k] = -1;
+    __syncthreads();
+    const int64_t span = (int64_t)blockDim.x * kHashBatch;
+    for (int64_t b0 = (int64_t)blockIdx.x * span; b0 < total; b0 += (int64_t)gridDim.x * span) {
+        for (int t = 0; t < kHashBatch; ++t) {
+            const int64_t s = b0 + (int64_t)t * blockDim.x + threadIdx.x;
+            if (s >= total)
+                break;
+            const int root = final_root(parent, (int)s, ordered, err);
+            if (root == (int)s)
+                continue;
+            const int mo = minorig[s];
+            uint32_t h = uf_priority(root) & (kHashSlots - 1);
+            bool placed = false;
+            for (int probe = 0; probe < kHashProbes; ++probe, h = (h + 1) & (kHashSlots - 1)) {
+                const int k = atomicCAS(&hkey[h], -1, root);
+                if (k == -1 || k == root) {
+                    if (k == -1) {            // the first insert initialises the entry
+                        hcnt[h] = 0;
+                        hmin[h] = INT_MAX;
+                    }
+                    placed = true;
+                    break;
+                }
+            }
+            if (!placed) {                    // no room on the probe path: add directly
+                atomicAdd(cnt + root, 1);
+                atomicMin(minorig + root, mo);
+            }
+            // entries are counted in the second pass, after every entry of
+            // the batch has been initialised
+        }
+        __syncthreads();
+        // second pass over the same slots: the table entries are initialised
+        for (int t = 0; t < kHashBatch; ++t) {
+            const int64_t s = b0 + (int64_t)t * blockDim.x + threadIdx.x;
+            if (s >= total)
+                break;
+            const int root = parent[s];   // fully compressed by the first pass
+            if (root == (int)s)
+                continue;
+            uint32_t h = uf_priority(root) & (kHashSlots - 1);
+            for (int probe = 0; probe < kHashProbes; ++probe, h = (h + 1) & (kHashSlots - 1)) {
+                if (hkey[h] == root) {
+                    atomicAdd(&hcnt[h], 1);
+                    atomicMin(&hmin[h], minorig[s]);
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) {
+            const int r = hkey[k];
+            if (r >= 0) {
+                atomicAdd(cnt + r, hcnt[k]);
+                atomicMin(minorig + r, hmin[k]);
+                hkey[k] = -1;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -262,12 +349,18 @@ static int grid_for(int64_t items, int threads, int per_sm)
     return (int)(want < cap ? want : cap);
 }
 
-cudaError_t launch_finalize(const Geometry& g, const Work& w, cudaStream_t s)
+cudaError_t launch_finalize(const Geometry& g, const Work& w, const UfArgs& uf, int size_count,
+                            cudaStream_t s)
 {
     if (g.total_n == 0)
         return cudaSuccess;
-    k_finalize<<<grid_for(g.total_n, 256, 8), 256, 0, s>>>(g.total_n, w.parent, w.minorig, w.cnt,
-                                                          &w.status->err);
+    const bool ordered = uf.link == 0;
+    if (size_count == 1)
+        k_finalize_hash<<<grid_for(g.total_n, 256 * kHashBatch, 4), 256, 0, s>>>(
+            g.total_n, w.parent, w.minorig, w.cnt, &w.status->err, ordered);
+    else
+        k_finalize<<<grid_for(g.total_n, 256, 8), 256, 0, s>>>(g.total_n, w.parent, w.minorig, w.cnt,
+                                                              &w.status->err, ordered);
     return cudaGetLastError();
 }
 

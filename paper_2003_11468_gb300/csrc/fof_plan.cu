@@ -37,15 +37,15 @@ int sm_count()
 namespace {
 
 enum Phase {
-    kPhBinCount, kPhScanBricks, kPhBinScatter, kPhBrickSort, kPhTeamSelf, kPhDenseSelf, kPhDensePairs,
-    kPhLink, kPhFinalize, kPhOutputs, kPhCatalogue, kNumPhases
+    kPhBinCount, kPhScanBricks, kPhBinScatter, kPhBrickSort, kPhTeamSelf, kPhBigSort, kPhDenseSelf,
+    kPhDensePairs, kPhBigPairs, kPhLink, kPhFinalize, kPhOutputs, kPhCatalogue, kNumPhases
 };
 
 const char* kPhaseNames[kNumPhases] = {
-    "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "team_self", "dense_self", "dense_pairs",
-    "link", "finalize", "outputs", "catalogue",
+    "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "team_self", "big_sort", "dense_self",
+    "dense_pairs", "big_pairs", "link", "finalize", "outputs", "catalogue",
 };
-const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 2, 1, 1, 1, 1, 2, 4};
+const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 2, 1, 1, 1, 1, 1, 1, 2, 4};
 
 constexpr int64_t kMaxTotal = 2147483646LL;   // slots and labels are int32
 constexpr int kDefaultRetryCap = 1 << 20;
@@ -111,6 +111,28 @@ float float_down(double v)      // largest float <= v
 //   sf < (l_x (1 - 2^-50) - 1.733 E)^2 (1 - 3.01 u)  =>  linked exactly.
 // Both bounds get a further relative slack of 2^-20 and are rounded outward
 // to float32.  Pairs between them take the exact double test.
+// Cells per brick side for nc cells per axis.
+int brick_side(int64_t nc)
+{
+    return nc >= 128 ? 16 : (nc >= 32 ? 8 : (nc >= 8 ? 4 : (nc >= 4 ? 2 : 1)));
+}
+
+// Sub-cells per cell side for nc cells per axis (1: the cells cannot be
+// split).  The conditions are derived below, at the sub-cell comment of
+// setup_box.
+int sub_cells_for(double L, double l_x, int64_t nc)
+{
+    const double h = L / (double)nc;
+    const double want = std::ceil(h * std::sqrt(3.0) * (1.0 + std::ldexp(1.0, -7)) / l_x);
+    if (want >= 2.0 && want <= kMaxQ && nc >= 3 && nc * (int64_t)want <= kMaxFinePerAxis) {
+        const double hf = h / want;
+        if (hf >= l_x * (1.0 + std::ldexp(1.0, -7)) / 2.0 &&
+            hf * std::sqrt(3.0) * (1.0 + std::ldexp(1.0, -7)) <= l_x)
+            return (int)want;
+    }
+    return 1;
+}
+
 int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
 {
     if (!std::isfinite(L) || !(L > 0.0) || !std::isfinite(l_x) || !(l_x > 0.0) ||
@@ -142,12 +164,38 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
         if ((r & (r - 1)) != 0 || r > 16 || r > nc)
             return FOF_ERR_ARG;
     } else {
-        r = nc >= 128 ? 16 : (nc >= 32 ? 8 : (nc >= 8 ? 4 : (nc >= 4 ? 2 : 1)));
+        r = brick_side(nc);
+    }
+    int64_t nb = nc / r;
+    nc = nb * r;
+    // The library's own cell count: when those cells cannot be split into
+    // sub-cells (their side falls between the ranges some q covers), take
+    // the nearest coarser grid (then finer) whose cells can, so that dense
+    // cells get the sub-cell method instead of pair-by-pair linking.
+    if (!(o && o->cells_per_axis > 0) && nc >= 3 && sub_cells_for(L, l_x, nc) == 1) {
+        for (int64_t d = 1; d <= nc; ++d) {
+            bool found = false;
+            for (int sgn = 0; sgn < 2 && !found; ++sgn) {
+                const int64_t c = sgn == 0 ? nc - d : nc + d;
+                if (c < 3 || c > nc_max)
+                    continue;
+                const int rc = (o && o->brick_cells > 0) ? r : brick_side(c);
+                if (rc > c)
+                    continue;
+                const int64_t cr = (c / rc) * rc;
+                if (cr >= 3 && cr <= nc_max && sub_cells_for(L, l_x, cr) > 1) {
+                    nc = cr;
+                    r = rc;
+                    nb = cr / rc;
+                    found = true;
+                }
+            }
+            if (found)
+                break;
+        }
     }
     int log2r = 0;
     while ((1 << log2r) < r) ++log2r;
-    int64_t nb = nc / r;
-    nc = nb * r;
 
     // Sub-cells.  q sub-cells per cell side, fine side hf = h/q with
     //   l_x (1 + 2^-7) / 2 <= hf <= l_x / (sqrt(3) (1 + 2^-7)),
@@ -160,17 +208,7 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
     // axis, has fine indices at most 2 apart, hence cell indices at most 1
     // apart.  When no q meets these bounds the box keeps q = 1 and cells
     // are never split.
-    int qs = 1;
-    {
-        double h = L / (double)nc;
-        double want = std::ceil(h * std::sqrt(3.0) * (1.0 + std::ldexp(1.0, -7)) / l_x);
-        if (want >= 2.0 && want <= kMaxQ && nc >= 3 && nc * (int64_t)want <= kMaxFinePerAxis) {
-            double hf = h / want;
-            if (hf >= l_x * (1.0 + std::ldexp(1.0, -7)) / 2.0 &&
-                hf * std::sqrt(3.0) * (1.0 + std::ldexp(1.0, -7)) <= l_x)
-                qs = (int)want;
-        }
-    }
+    const int qs = sub_cells_for(L, l_x, nc);
     b.n = n;
     b.L = L;
     b.l2 = l_x * l_x;
@@ -299,7 +337,12 @@ struct fof_plan {
     ResultsLayout rl{};
     int dense_min = kDefaultDenseMin;
     int retry_cap = kDefaultRetryCap;
+    int find_variant = 0;
+    int link_order = 0;
+    int size_count = 0;
     bool linked = false;
+    bool binned = false;      // the binned order of the last fof_link is in place
+    int last_relink_path = -1;
     bool pending = false;
     int64_t last_cap = 0;
     bool timing = false;
@@ -312,6 +355,15 @@ struct fof_plan {
     int32_t* sizes_d = nullptr;
     int2* cat_d = nullptr;
     int64_t cat_d_cap = 0;
+    // fof_run_host_many: two staging sets, copy streams and their events
+    float* pos2[2] = {nullptr, nullptr};
+    int32_t* ids2[2] = {nullptr, nullptr};
+    int32_t* sizes2[2] = {nullptr, nullptr};
+    int2* cat2[2] = {nullptr, nullptr};
+    int64_t cat2_cap = 0;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+                ev_d2h[2] = {nullptr, nullptr};
     // graph
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_cap = 0;
@@ -322,7 +374,7 @@ namespace {
 struct Layout {
     size_t boxes, p0, brick0, results, bcount, bstart, bcursor, scan_tmp, tile_cnt, tile_off,
         cell_start, tmp, sorted, parent, minorig, cnt, dense_list, n_dense, dense_root, out_cursor,
-        team_list, n_team, total;
+        team_list, n_team, big_list, n_big, total;
     int64_t scan_len, n_tiles, dense_cap;
 };
 
@@ -362,6 +414,8 @@ Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cel
     L.out_cursor = take(4 * (size_t)((total_n >> kOutChunkLog) + 2));
     L.team_list = take(8 * (size_t)(total_n / kMinTeamMin + 1));
     L.n_team = take(4);
+    L.big_list = take(8 * (size_t)(total_n / (kDenseMax + 1) + 1));
+    L.n_big = take(4);
     L.total = off;
     return L;
 }
@@ -466,6 +520,11 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     if (opt && opt->retry_cap > 0) h->retry_cap = opt->retry_cap;
     // the retry-cap test: a union that must hook gives up before its first CAS
     if (opt && (opt->debug_flags & FOF_DEBUG_UNION_NO_RETRY)) h->retry_cap = 0;
+    if (opt) {
+        h->find_variant = opt->find_variant;
+        h->link_order = opt->link_order;
+        h->size_count = opt->size_count;
+    }
     h->rl = results_layout(nbox);
     if (workspace) {
         h->ws = (char*)workspace;
@@ -533,6 +592,8 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     w.out_cursor = (int*)(ws + L.out_cursor);
     w.team_list = (int64_t*)(ws + L.team_list);
     w.n_team = (int*)(ws + L.n_team);
+    w.big_list = (int64_t*)(ws + L.big_list);
+    w.n_big = (int*)(ws + L.n_big);
 
     cudaError_t e = cudaMemcpy(ws + L.boxes, boxes.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -547,10 +608,50 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     return FOF_OK;
 }
 
+UfArgs uf_args(const fof_plan* h)
+{
+    UfArgs u;
+    u.cap = h->retry_cap;
+    u.err = &h->w.status->err;
+    u.find = h->find_variant;
+    u.link = h->link_order;
+    return u;
+}
+
+// Linking on the binned particles: self tasks of team cells, dense cells,
+// then the rest (shared by fof_link and fof_relink).
+int enqueue_linking(fof_plan* h, cudaStream_t s)
+{
+    const Geometry& g = h->g;
+    const Work& w = h->w;
+    const UfArgs uf = uf_args(h);
+    phase_begin(h, kPhTeamSelf, s);
+    FOF_TRY(launch_team_self(g, w, s));
+    phase_end(h, kPhTeamSelf, s);
+    phase_begin(h, kPhBigSort, s);
+    FOF_TRY(launch_big(g, w, h->dense_min, uf, false, s));
+    phase_end(h, kPhBigSort, s);
+    phase_begin(h, kPhDenseSelf, s);
+    FOF_TRY(launch_dense(g, w, h->dense_min, uf, false, s));
+    phase_end(h, kPhDenseSelf, s);
+    phase_begin(h, kPhDensePairs, s);
+    FOF_TRY(launch_dense(g, w, h->dense_min, uf, true, s));
+    phase_end(h, kPhDensePairs, s);
+    phase_begin(h, kPhBigPairs, s);
+    FOF_TRY(launch_big(g, w, h->dense_min, uf, true, s));
+    phase_end(h, kPhBigPairs, s);
+    phase_begin(h, kPhLink, s);
+    FOF_TRY(launch_link(g, w, h->dense_min, uf, s));
+    phase_end(h, kPhLink, s);
+    h->linked = true;
+    return FOF_OK;
+}
+
 int enqueue_link(fof_plan* h, const float* pos, cudaStream_t s)
 {
     const Geometry& g = h->g;
     const Work& w = h->w;
+    const UfArgs uf = uf_args(h);
     FOF_TRY(cudaMemsetAsync(h->results_dev, 0, h->rl.bytes, s));
     if (g.total_n == 0) {
         h->linked = true;
@@ -569,22 +670,14 @@ int enqueue_link(fof_plan* h, const float* pos, cudaStream_t s)
     phase_end(h, kPhBinScatter, s);
     FOF_TRY(cudaMemsetAsync(w.n_dense, 0, 4, s));
     FOF_TRY(cudaMemsetAsync(w.n_team, 0, 4, s));
+    FOF_TRY(cudaMemsetAsync(w.n_big, 0, 4, s));
     phase_begin(h, kPhBrickSort, s);
     FOF_TRY(launch_brick_sort(g, w, h->dense_min, s));
     phase_end(h, kPhBrickSort, s);
-    phase_begin(h, kPhTeamSelf, s);
-    FOF_TRY(launch_team_self(g, w, s));
-    phase_end(h, kPhTeamSelf, s);
-    phase_begin(h, kPhDenseSelf, s);
-    FOF_TRY(launch_dense(g, w, h->dense_min, h->retry_cap, false, s));
-    phase_end(h, kPhDenseSelf, s);
-    phase_begin(h, kPhDensePairs, s);
-    FOF_TRY(launch_dense(g, w, h->dense_min, h->retry_cap, true, s));
-    phase_end(h, kPhDensePairs, s);
-    phase_begin(h, kPhLink, s);
-    FOF_TRY(launch_link(g, w, h->dense_min, h->retry_cap, s));
-    phase_end(h, kPhLink, s);
-    h->linked = true;
+    int rc_ = enqueue_linking(h, s);
+    if (rc_ != FOF_OK)
+        return rc_;
+    h->binned = true;
     return FOF_OK;
 }
 
@@ -600,7 +693,7 @@ int enqueue_groups(fof_plan* h, int32_t* ids, int32_t* sizes, fof_group* cat, in
         FOF_TRY(cudaMemsetAsync(w.tile_cnt, 0, 4 * (size_t)(w.n_tiles + 1), s));
         FOF_TRY(cudaMemsetAsync(w.out_cursor, 0, 4 * (size_t)((g.total_n >> kOutChunkLog) + 2), s));
         phase_begin(h, kPhFinalize, s);
-        FOF_TRY(launch_finalize(g, w, s));
+        FOF_TRY(launch_finalize(g, w, uf_args(h), h->size_count, s));
         phase_end(h, kPhFinalize, s);
         phase_begin(h, kPhOutputs, s);
         FOF_TRY(launch_outputs(g, w, ids, sizes, min_size, s));
@@ -699,6 +792,58 @@ int fof_link(fof_handle h, const float* pos_dev, void* stream)
     return enqueue_link(h, pos_dev, (cudaStream_t)stream);
 }
 
+int fof_relink(fof_handle h, const float* pos_dev, int32_t* path_out, void* stream)
+{
+    if (!h || (h->g.total_n > 0 && !pos_dev))
+        return FOF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geometry& g = h->g;
+    const Work& w = h->w;
+    int path = 2;
+    if (h->binned && !h->capturing && g.total_n > 0) {
+        // which particles left their cell or brick: one flag word, read back
+        FOF_TRY(cudaMemsetAsync(h->results_dev, 0, h->rl.bytes, s));
+        phase_begin(h, kPhBinCount, s);
+        FOF_TRY(launch_relink_check(pos_dev, g, w, &w.status->pad, s));
+        phase_end(h, kPhBinCount, s);
+        FOF_TRY(cudaMemcpyAsync(h->results_host, h->results_dev, sizeof(Status), cudaMemcpyDeviceToHost, s));
+        FOF_TRY(cudaStreamSynchronize(s));
+        const Status* st = (const Status*)h->results_host;
+        if (st->err == 0 && (st->pad & 2) == 0)
+            path = (st->pad & 1) ? 1 : 0;
+    }
+    h->binned = false;
+    if (path == 2) {
+        int rc = enqueue_link(h, pos_dev, s);
+        if (rc != FOF_OK)
+            return rc;
+    } else {
+        if (path == 1) {
+            // every particle kept its brick: the slots are still grouped by
+            // brick, so the per-brick cell sort runs on the new positions
+            FOF_TRY(cudaMemsetAsync(w.n_dense, 0, 4, s));
+            FOF_TRY(cudaMemsetAsync(w.n_team, 0, 4, s));
+            FOF_TRY(cudaMemsetAsync(w.n_big, 0, 4, s));
+            phase_begin(h, kPhBrickSort, s);
+            FOF_TRY(launch_brick_sort(g, w, h->dense_min, s));
+            phase_end(h, kPhBrickSort, s);
+        } else {
+            // every particle kept its cell: cells, starts and lists stand
+            phase_begin(h, kPhBrickSort, s);
+            FOF_TRY(launch_forest_init(g, w, s));
+            phase_end(h, kPhBrickSort, s);
+        }
+        int rc = enqueue_linking(h, s);
+        if (rc != FOF_OK)
+            return rc;
+        h->binned = true;
+    }
+    h->last_relink_path = path;
+    if (path_out)
+        *path_out = path;
+    return FOF_OK;
+}
+
 int fof_groups_async(fof_handle h, int32_t* ids_dev, int32_t* sizes_dev, fof_group* catalogue_dev,
                      int64_t cat_capacity, int32_t min_size, void* stream)
 {
@@ -783,6 +928,112 @@ int fof_run_host(fof_handle h, const float* pos_host, int32_t* ids_host, int32_t
         if (n_cat_out) n_cat_out[i] = nk[i];
     }
     return rc;
+}
+
+int fof_run_host_many(fof_handle h, int32_t nsteps, const float* const* pos_host, int32_t* const* ids_host,
+                      int32_t* const* sizes_host, fof_group* const* catalogue_host, int64_t cat_capacity,
+                      int32_t min_size, int64_t* n_groups_out, int64_t* n_cat_out, void* stream)
+{
+    if (!h || nsteps < 0 || cat_capacity < 0 || (nsteps > 0 && (!pos_host || !ids_host || !sizes_host)) ||
+        (cat_capacity > 0 && !catalogue_host))
+        return FOF_ERR_ARG;
+    const int64_t n = h->g.total_n;
+    for (int k = 0; k < nsteps; ++k)
+        if ((n > 0 && (!pos_host[k] || !ids_host[k] || !sizes_host[k])) ||
+            (cat_capacity > 0 && !catalogue_host[k]))
+            return FOF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // staging, streams and events on first use (kept by the handle)
+    if (!h->copy_in) {
+        FOF_TRY(cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking));
+        FOF_TRY(cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            FOF_TRY(cudaEventCreateWithFlags(&h->ev_h2d[b], cudaEventDisableTiming));
+            FOF_TRY(cudaEventCreateWithFlags(&h->ev_comp[b], cudaEventDisableTiming));
+            FOF_TRY(cudaEventCreateWithFlags(&h->ev_d2h[b], cudaEventDisableTiming));
+        }
+    }
+    for (int b = 0; b < 2 && n > 0; ++b)
+        if (!h->pos2[b]) {
+            if (cudaMalloc((void**)&h->pos2[b], 12 * (size_t)n) != cudaSuccess ||
+                cudaMalloc((void**)&h->ids2[b], 4 * (size_t)n) != cudaSuccess ||
+                cudaMalloc((void**)&h->sizes2[b], 4 * (size_t)n) != cudaSuccess) {
+                cudaGetLastError();
+                return FOF_ERR_OOM;
+            }
+        }
+    if (cat_capacity > h->cat2_cap) {
+        FOF_TRY(cudaDeviceSynchronize());       // the old catalogue buffers may be in use
+        for (int b = 0; b < 2; ++b) {
+            if (h->cat2[b]) cudaFree(h->cat2[b]);
+            h->cat2[b] = nullptr;
+        }
+        h->cat2_cap = 0;
+        for (int b = 0; b < 2; ++b)
+            if (cudaMalloc((void**)&h->cat2[b], 8 * (size_t)cat_capacity) != cudaSuccess) {
+                cudaGetLastError();
+                return FOF_ERR_OOM;
+            }
+        h->cat2_cap = cat_capacity;
+    }
+    auto drain = [&]() {
+        cudaStreamSynchronize(h->copy_in);
+        cudaStreamSynchronize(s);
+        cudaStreamSynchronize(h->copy_out);
+    };
+    auto h2d = [&](int k) -> cudaError_t {
+        const int b = k & 1;
+        // the buffer was last read by step k - 2's binning
+        cudaError_t e = cudaStreamWaitEvent(h->copy_in, h->ev_comp[b], 0);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(h->pos2[b], pos_host[k], 12 * (size_t)n, cudaMemcpyHostToDevice, h->copy_in);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(h->ev_h2d[b], h->copy_in);
+        return e;
+    };
+    int result = FOF_OK;
+    if (nsteps > 0) {
+        cudaError_t e = h2d(0);
+        if (e != cudaSuccess) { drain(); return cuda_rc(e); }
+    }
+    std::vector<int64_t> ng(h->nbox), nk(h->nbox);
+    for (int k = 0; k < nsteps; ++k) {
+        const int b = k & 1;
+        cudaError_t e = cudaSuccess;
+        if (k + 1 < nsteps)
+            e = h2d(k + 1);                      // the next input moves while this one runs
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_h2d[b], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_d2h[b], 0);   // step k - 2's outputs are out
+        if (e != cudaSuccess) { drain(); return cuda_rc(e); }
+        int rc = enqueue_link(h, h->pos2[b], s);
+        if (rc == FOF_OK)
+            rc = enqueue_groups(h, h->ids2[b], h->sizes2[b], (fof_group*)h->cat2[b], cat_capacity, min_size, s);
+        if (rc == FOF_OK && cudaEventRecord(h->ev_comp[b], s) != cudaSuccess)
+            rc = FOF_ERR_CUDA;
+        if (rc != FOF_OK) { drain(); return rc; }
+        rc = read_result(h, ng.data(), nk.data(), s);
+        if (rc != FOF_OK && rc != FOF_ERR_CAPACITY) { drain(); return rc; }
+        if (rc == FOF_ERR_CAPACITY)
+            result = FOF_ERR_CAPACITY;
+        const Status* st = (const Status*)(h->results_host + h->rl.status_off);
+        const int64_t ncopy = st->n_cat_total < cat_capacity ? st->n_cat_total : cat_capacity;
+        e = cudaStreamWaitEvent(h->copy_out, h->ev_comp[b], 0);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(ids_host[k], h->ids2[b], 4 * (size_t)n, cudaMemcpyDeviceToHost, h->copy_out);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(sizes_host[k], h->sizes2[b], 4 * (size_t)n, cudaMemcpyDeviceToHost, h->copy_out);
+        if (e == cudaSuccess && ncopy > 0)
+            e = cudaMemcpyAsync(catalogue_host[k], h->cat2[b], 8 * (size_t)ncopy, cudaMemcpyDeviceToHost,
+                                h->copy_out);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_d2h[b], h->copy_out);
+        if (e != cudaSuccess) { drain(); return cuda_rc(e); }
+        for (int i = 0; i < h->nbox; ++i) {
+            if (n_groups_out) n_groups_out[(int64_t)k * h->nbox + i] = ng[i];
+            if (n_cat_out) n_cat_out[(int64_t)k * h->nbox + i] = nk[i];
+        }
+    }
+    FOF_TRY(cudaStreamSynchronize(h->copy_out));
+    return result;
 }
 
 int fof_graph_build(fof_handle h, const float* pos_dev, int32_t* ids_dev, int32_t* sizes_dev,
@@ -922,6 +1173,17 @@ void fof_destroy(fof_handle h)
         if (h->phase[k].ev0) cudaEventDestroy(h->phase[k].ev0);
         if (h->phase[k].ev1) cudaEventDestroy(h->phase[k].ev1);
     }
+    for (int b = 0; b < 2; ++b) {
+        if (h->pos2[b]) cudaFree(h->pos2[b]);
+        if (h->ids2[b]) cudaFree(h->ids2[b]);
+        if (h->sizes2[b]) cudaFree(h->sizes2[b]);
+        if (h->cat2[b]) cudaFree(h->cat2[b]);
+        if (h->ev_h2d[b]) cudaEventDestroy(h->ev_h2d[b]);
+        if (h->ev_comp[b]) cudaEventDestroy(h->ev_comp[b]);
+        if (h->ev_d2h[b]) cudaEventDestroy(h->ev_d2h[b]);
+    }
+    if (h->copy_in) cudaStreamDestroy(h->copy_in);
+    if (h->copy_out) cudaStreamDestroy(h->copy_out);
     if (h->pos_d) cudaFree(h->pos_d);
     if (h->ids_d) cudaFree(h->ids_d);
     if (h->sizes_d) cudaFree(h->sizes_d);
@@ -1049,6 +1311,8 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
     w.out_cursor = (int*)(ws + L.out_cursor);
     w.team_list = (int64_t*)(ws + L.team_list);
     w.n_team = (int*)(ws + L.n_team);
+    w.big_list = (int64_t*)(ws + L.big_list);
+    w.n_big = (int*)(ws + L.n_big);
 
     // The array keeps the previous call's contents: the box table is
     // rewritten and every counter that must start at zero is cleared here.
@@ -1067,12 +1331,20 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
         FOF_TRY(launch_scan(w.bcount, w.bstart, tb, w.scan_tmp, w.scan_tmp_len, s));
         FOF_TRY(launch_bin_scatter(pos_dev, g, w, s));
         FOF_TRY(cudaMemsetAsync(w.n_team, 0, 4, s));
+        FOF_TRY(cudaMemsetAsync(w.n_big, 0, 4, s));
         FOF_TRY(launch_brick_sort(g, w, kDefaultDenseMin, s));
         FOF_TRY(launch_team_self(g, w, s));
-        FOF_TRY(launch_dense(g, w, kDefaultDenseMin, kDefaultRetryCap, false, s));
-        FOF_TRY(launch_dense(g, w, kDefaultDenseMin, kDefaultRetryCap, true, s));
-        FOF_TRY(launch_link(g, w, kDefaultDenseMin, kDefaultRetryCap, s));
-        FOF_TRY(launch_finalize(g, w, s));
+        UfArgs uf;
+        uf.cap = kDefaultRetryCap;
+        uf.err = &w.status->err;
+        uf.find = 0;
+        uf.link = 0;
+        FOF_TRY(launch_big(g, w, kDefaultDenseMin, uf, false, s));
+        FOF_TRY(launch_dense(g, w, kDefaultDenseMin, uf, false, s));
+        FOF_TRY(launch_dense(g, w, kDefaultDenseMin, uf, true, s));
+        FOF_TRY(launch_big(g, w, kDefaultDenseMin, uf, true, s));
+        FOF_TRY(launch_link(g, w, kDefaultDenseMin, uf, s));
+        FOF_TRY(launch_finalize(g, w, uf, 0, s));
         FOF_TRY(launch_outputs(g, w, ids_dev, sizes_dev, min_size, s));
         FOF_TRY(launch_catalogue(g, w, sizes_dev, min_size, (int2*)catalogue_dev, cat_capacity, s));
     }

@@ -98,10 +98,12 @@ def load():
             "fof_batch_create": ([i32, P, P, P, P, P, sz, PP], ctypes.c_int),
             "fof_batch_workspace_bytes": ([i32, P, P, P, P], sz),
             "fof_link": ([P, P, P], ctypes.c_int),
+            "fof_relink": ([P, P, P, P], ctypes.c_int),
             "fof_groups": ([P, P, P, P, i64, i32, P, P, P], ctypes.c_int),
             "fof_groups_async": ([P, P, P, P, i64, i32, P], ctypes.c_int),
             "fof_result": ([P, P, P, P], ctypes.c_int),
             "fof_run_host": ([P, P, P, P, P, i64, i32, P, P, P], ctypes.c_int),
+            "fof_run_host_many": ([P, i32, P, P, P, P, i64, i32, P, P, P], ctypes.c_int),
             "fof_graph_build": ([P, P, P, P, P, i64, i32, P], ctypes.c_int),
             "fof_graph_launch": ([P, P], ctypes.c_int),
             "fof_plan_info": ([P, i32, P, P, P], ctypes.c_int),
@@ -113,6 +115,7 @@ def load():
             "fof_destroy": ([P], None),
             "fof_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "fof_run_noalloc": ([f64, f64, i64, P, P, P, P, i64, i32, P, P, P], ctypes.c_int),
+            "fof_merge_links": ([i64, P, P, i64, P, P, i64, P, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -205,6 +208,13 @@ def fof_link(h, pos, stream=None) -> int:
     return _check(load().fof_link(h, _ptr(pos), _stream(stream)), "fof_link")
 
 
+def fof_relink(h, pos, stream=None) -> int:
+    """fof_link for moved particles; returns the path taken (0, 1 or 2)."""
+    path = ctypes.c_int32(-1)
+    _check(load().fof_relink(h, _ptr(pos), ctypes.byref(path), _stream(stream)), "fof_relink")
+    return path.value
+
+
 def fof_groups(h, ids, sizes, catalogue, cat_capacity, min_size, nbox=1, stream=None,
                allow_capacity=False):
     """Returns (code, n_groups[list], n_cat[list])."""
@@ -240,6 +250,25 @@ def fof_run_host(h, pos_host, ids_host, sizes_host, cat_host, cat_capacity, min_
     if code != FOF_OK and not (allow_capacity and code == FOF_ERR_CAPACITY):
         raise FoFError(code, "fof_run_host")
     return code, list(ng), list(nk)
+
+
+def fof_run_host_many(h, pos_hosts, ids_hosts, sizes_hosts, cat_hosts, cat_capacity, min_size, nbox=1,
+                      stream=None, allow_capacity=False):
+    """fof_run_host over several inputs with overlapped copies; returns
+    (code, n_groups[nsteps][nbox], n_cat[nsteps][nbox])."""
+    k = len(pos_hosts)
+    VP = ctypes.c_void_p * max(k, 1)
+    pp = VP(*[_ptr(x) for x in pos_hosts])
+    ip = VP(*[_ptr(x) for x in ids_hosts])
+    sp = VP(*[_ptr(x) for x in sizes_hosts])
+    cp = VP(*[_ptr(x) for x in cat_hosts]) if cat_hosts is not None else None
+    ng = (ctypes.c_int64 * max(k * nbox, 1))()
+    nk = (ctypes.c_int64 * max(k * nbox, 1))()
+    code = load().fof_run_host_many(h, k, pp, ip, sp, cp, cat_capacity, min_size, ng, nk, _stream(stream))
+    if code != FOF_OK and not (allow_capacity and code == FOF_ERR_CAPACITY):
+        raise FoFError(code, "fof_run_host_many")
+    return (code, [list(ng[i * nbox:(i + 1) * nbox]) for i in range(k)],
+            [list(nk[i * nbox:(i + 1) * nbox]) for i in range(k)])
 
 
 def fof_graph_build(h, pos, ids, sizes, catalogue, cat_capacity, min_size, stream) -> int:
@@ -306,6 +335,24 @@ def fof_run_noalloc(box, l_x, n, pos, ids, sizes, catalogue, cat_capacity, min_s
     if code != FOF_OK and not (allow_capacity and code == FOF_ERR_CAPACITY):
         raise FoFError(code, "fof_run_noalloc")
     return code, ng.value, nk.value
+
+
+def fof_merge_links(a, b, query, weight_ids=None, weights=None, want_weights=False):
+    """Union-find over gathered links (int64 numpy arrays); returns the
+    smallest id of each query's merged set (and the set weights)."""
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    b = np.ascontiguousarray(b, dtype=np.int64)
+    q = np.ascontiguousarray(query, dtype=np.int64)
+    wi = np.ascontiguousarray(weight_ids if weight_ids is not None else np.zeros(0), dtype=np.int64)
+    wv = np.ascontiguousarray(weights if weights is not None else np.zeros(0), dtype=np.int64)
+    assert a.shape == b.shape and wi.shape == wv.shape
+    lab = np.empty(q.shape[0], dtype=np.int64)
+    wout = np.empty(q.shape[0], dtype=np.int64) if want_weights else None
+    _check(load().fof_merge_links(a.shape[0], _ptr(a), _ptr(b), wi.shape[0], _ptr(wi), _ptr(wv),
+                                  q.shape[0], _ptr(q), _ptr(lab), _ptr(wout) if wout is not None else None),
+           "fof_merge_links")
+    return (lab, wout) if want_weights else lab
 
 
 # ---------------------------------------------------------------------------

@@ -132,3 +132,32 @@ def test_server_admission_and_oversize(cuda_lib):
     for r, (p, b, l) in zip(res, boxes):
         wid, wsz = oracle.groups(p, b, l)
         assert np.array_equal(r.ids, wid) and np.array_equal(r.sizes, wsz)
+
+
+def test_server_budget_covers_retained_buffers(cuda_lib):
+    """The budget bounds what the slots keep, idle or busy: after a large
+    request the slots' retained buffers plus later small batches stay within
+    it, and the process's reserved device memory grows by no more than the
+    budget."""
+    import torch
+    fof = cuda_lib
+    from paper_2003_11468_gb300.server import Server
+    big = _boxes(1, seed=5, n_lo=400000, n_hi=400001)[0]
+    small = _boxes(12, seed=6, n_lo=20000, n_hi=60000)
+    need_big = fof.fof_batch_workspace_bytes([big[1]], [big[2]], [big[0].shape[0]]) + 28 * big[0].shape[0]
+    budget = int(need_big * 1.6)                 # room for one big slot, not two
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    base = torch.cuda.memory_reserved()
+    with Server(memory_budget=budget, slots=3) as srv:
+        r0 = srv.submit(torch.from_numpy(big[0]).pin_memory(), big[1], big[2], 5).result(timeout=120)
+        futs = [srv.submit(torch.from_numpy(p).pin_memory(), b, l, 5) for p, b, l in small]
+        res = [f.result(timeout=120) for f in futs]
+        r1 = srv.submit(torch.from_numpy(big[0]).pin_memory(), big[1], big[2], 5).result(timeout=120)
+        assert srv.held_bytes() <= budget
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_reserved() - base <= budget + (64 << 20)
+    assert np.array_equal(r0.ids, r1.ids)
+    for r, (p, b, l) in zip(res, small):
+        wid, wsz = oracle.groups(p, b, l)
+        assert np.array_equal(r.ids, wid) and np.array_equal(r.sizes, wsz)

@@ -442,3 +442,182 @@ def test_tie_rule_option(cuda_lib, seed):
         wid, wsz = oracle.groups(pos, 1.0, g, strict=strict)
         assert np.array_equal(ids.cpu().numpy(), wid), strict
         assert np.array_equal(sizes.cpu().numpy(), wsz), strict
+
+
+@pytest.mark.parametrize("find,link,size", [
+    (0, 0, 1), (1, 0, 0), (2, 0, 0), (3, 0, 0),
+    (0, 1, 0), (1, 1, 1), (2, 1, 0), (3, 1, 1),
+])
+def test_union_find_variants(cuda_lib, find, link, size):
+    """Every union-find variant of fof.h (compression of Find, Sec. 3.4.3;
+    randomised linking, Sec. 3.2; hash-table size count, Sec. 3.4.1) gives
+    exactly the oracle's partition, sizes and catalogue on a clustered box
+    with dense, team and sparse cells."""
+    torch = _torch()
+    fof = cuda_lib
+    n, box = 300000, 30.0
+    pos = synth.clustered_box(n, box, 120, seed=700 + 10 * find + 3 * link + size)
+    l_x = synth.linking_length(n, box, 0.25)
+    opt = fof.fof_options()
+    opt.find_variant, opt.link_order, opt.size_count = find, link, size
+    with fof.FoF(box, l_x, n, opt) as f:
+        ids, sizes, cat, ng = f.run(torch.from_numpy(pos).cuda(), min_size=10)
+    wid, wsz = oracle.groups(pos, box, l_x)
+    assert np.array_equal(ids.cpu().numpy(), wid)
+    assert np.array_equal(sizes.cpu().numpy(), wsz)
+    assert np.array_equal(cat.cpu().numpy(), oracle.catalogue(wsz, 10))
+    assert ng == int((wsz > 0).sum())
+
+
+def test_relink_paths(cuda_lib):
+    """fof_relink on moved particles: every path gives the oracle's answer for
+    the new positions.  Unmoved particles take path 0 (cells re-used),
+    particles moved toward their cell's centre path 1 or 0 (no brick change
+    possible), large moves path 2 (full re-binning)."""
+    torch = _torch()
+    fof = cuda_lib
+    n, box = 200000, 25.0
+    pos = synth.clustered_box(n, box, 90, seed=811)
+    l_x = synth.linking_length(n, box, 0.3)
+    geo = fof.fof_box_geometry(box, l_x, n)
+    q, inv = geo.sub_cells, np.float32(geo.inv_fine)
+
+    def cells(p):
+        f = np.minimum((p * inv).astype(np.int32), geo.fine_per_axis - 1)
+        return f // q
+
+    # toward the cell centre by 30%: no particle crosses a cell face
+    c = cells(pos)
+    centre = ((c.astype(np.float64) + 0.5) * q / float(inv)).astype(np.float32)
+    near = (pos + np.float32(0.3) * (centre - pos)).astype(np.float32)
+    stay = (cells(near) == c).all(axis=1)
+    near[~stay] = pos[~stay]
+    rng = np.random.default_rng(3)
+    far = np.mod(pos + rng.normal(0, 0.4, pos.shape), box).astype(np.float32)
+    far[far >= np.float32(box)] = 0.0
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    sizes = torch.empty(n, dtype=torch.int32, device="cuda")
+    h = fof.fof_create(box, l_x, n)
+    try:
+        fof.fof_link(h, torch.from_numpy(pos).cuda())
+        fof.fof_groups(h, ids, sizes, None, 0, 1)
+        for p, allowed in ((pos, (0,)), (near, (0, 1)), (far, (2,)), (far, (0,)), (pos, (1, 2))):
+            dev = torch.from_numpy(np.ascontiguousarray(p)).cuda()
+            path = fof.fof_relink(h, dev)
+            assert path in allowed
+            fof.fof_groups(h, ids, sizes, None, 0, 1)
+            wid, wsz = oracle.groups(p, box, l_x)
+            assert np.array_equal(ids.cpu().numpy(), wid), path
+            assert np.array_equal(sizes.cpu().numpy(), wsz), path
+    finally:
+        fof.fof_destroy(h)
+
+
+def _big_cell_box(seed):
+    """One cell of side 6.5 l_x holding 50,000 particles in 8 tight blobs (a
+    2x2x2 lattice 3.25 l_x apart, so most stay separate groups), inside a
+    10^3-cell box with a sparse background and a blob straddling the big
+    cell's +x face."""
+    rng = np.random.default_rng(seed)
+    l_x, h, nc = 0.1, 0.65, 10
+    box = h * nc
+    lo = np.array([h, h, h])
+    g = np.array([[i, j, k] for i in (0.25, 0.75) for j in (0.25, 0.75) for k in (0.25, 0.75)])
+    cent = lo + g * h
+    inside = cent[rng.integers(0, 8, 50000)] + rng.normal(0, 0.2 * l_x, (50000, 3))
+    inside = np.clip(inside, lo, lo + h * (1 - 1e-6))
+    edge = np.array([2 * h, 1.5 * h, 1.5 * h]) + rng.normal(0, 0.4 * l_x, (3000, 3))
+    bg = rng.random((20000, 3)) * box
+    pos = np.mod(np.concatenate([inside, edge, bg]), box).astype(np.float32)
+    pos[pos >= np.float32(box)] = 0.0
+    return pos, box, l_x, nc
+
+
+def test_big_cell_sub_cell_path(cuda_lib):
+    """A cell of 50,000 particles (above the shared-memory dense range) is
+    linked by the big-cell kernels in sub-cell order: exact against the
+    oracle, and in well under a second (no pair-by-pair O(m^2) work)."""
+    import time
+    torch = _torch()
+    fof = cuda_lib
+    pos, box, l_x, nc = _big_cell_box(31)
+    n = pos.shape[0]
+    opt = fof.fof_options()
+    opt.cells_per_axis = nc
+    opt.brick_cells = 2
+    geo = fof.fof_box_geometry(box, l_x, n, opt)
+    assert geo.cells_per_axis == nc and geo.sub_cells > 1
+    dev = torch.from_numpy(pos).cuda()
+    with fof.FoF(box, l_x, n, opt) as f:
+        f.run(dev)                                    # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids, sizes, cat, ng = f.run(dev, min_size=20)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    wid, wsz = oracle.groups(pos, box, l_x)
+    assert np.array_equal(ids.cpu().numpy(), wid)
+    assert np.array_equal(sizes.cpu().numpy(), wsz)
+    assert np.array_equal(cat.cpu().numpy(), oracle.catalogue(wsz, 20))
+    assert dt < 1.0, dt
+
+
+@pytest.mark.parametrize("n,width", [(20000, 2.6), (8000, 2.9)])
+def test_box_without_splittable_cells(cuda_lib, n, width):
+    """A box fewer than 3 linking lengths wide has at most 2 cells per axis
+    and cannot be split into sub-cells: every pair is tested (O(n^2) work
+    spread over the warps); exact and bounded in time."""
+    import time
+    torch = _torch()
+    fof = cuda_lib
+    l_x = 0.05
+    box = width * l_x
+    rng = np.random.default_rng(n)
+    pos = (rng.random((n, 3)) * box).astype(np.float32)
+    pos[pos >= np.float32(box)] = 0.0
+    geo = fof.fof_box_geometry(box, l_x, n)
+    assert geo.sub_cells == 1 and geo.cells_per_axis < 3
+    dev = torch.from_numpy(pos).cuda()
+    with fof.FoF(box, l_x, n) as f:
+        f.run(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids, sizes, _, _ = f.run(dev)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    wid, wsz = oracle.groups(pos, box, l_x)
+    assert np.array_equal(ids.cpu().numpy(), wid)
+    assert np.array_equal(sizes.cpu().numpy(), wsz)
+    assert dt < 1.0, dt
+
+
+def test_run_host_many_pipelined(cuda_lib):
+    """fof_run_host_many: several host inputs of one plan, copies overlapped
+    with compute on separate streams; every step's ids, sizes, catalogue and
+    counts equal the oracle's for that step's input."""
+    torch = _torch()
+    fof = cuda_lib
+    n, box = 120000, 20.0
+    l_x = synth.linking_length(n, box)
+    inputs = [synth.clustered_box(n, box, 40 + 10 * k, seed=950 + k) for k in range(4)]
+    pos_h = [torch.from_numpy(p).pin_memory() for p in inputs]
+    ids_h = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in inputs]
+    sizes_h = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in inputs]
+    cap = 5000
+    cat_h = [torch.empty((cap, 2), dtype=torch.int32).pin_memory() for _ in inputs]
+    stream = torch.cuda.Stream()
+    h = fof.fof_create(box, l_x, n)
+    try:
+        for _ in range(2):                     # the second call re-uses the staging
+            code, ng, nk = fof.fof_run_host_many(h, pos_h, ids_h, sizes_h, cat_h, cap, 10, 1, stream)
+            assert code == 0
+            for k, p in enumerate(inputs):
+                wid, wsz = oracle.groups(p, box, l_x)
+                wcat = oracle.catalogue(wsz, 10)
+                assert np.array_equal(ids_h[k].numpy(), wid), k
+                assert np.array_equal(sizes_h[k].numpy(), wsz), k
+                assert nk[k][0] == wcat.shape[0] and ng[k][0] == int((wsz > 0).sum())
+                assert np.array_equal(cat_h[k].numpy()[: nk[k][0]], wcat)
+                ids_h[k].fill_(-1)
+    finally:
+        fof.fof_destroy(h)
