@@ -708,6 +708,133 @@ def run_served(args):
     return 0
 
 
+def run_ablation(args):
+    """The paper's union-find alternatives (fof.h variant fields) timed on one
+    workload: each variant runs the same input, its ids are checked equal to
+    the default's (or, for the strict tie rule, reported as differing), and
+    the per-phase device times are reported.  One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2003_11468_gb300 import fof
+    fof.load()
+    wl = workloads()[args.workload]()
+    pos = torch.from_numpy(wl["make"]()).cuda()
+    n, box, l_x = wl["n"], wl["box"], wl["l_x"]
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    sizes = torch.empty_like(ids)
+    ref = None
+    variants = [
+        ("default: halving on paths of depth >= 2, hook onto the smaller root, warp-aggregated sizes", {}),
+        ("find: halving at every depth", {"find_variant": 1}),
+        ("find: full compression", {"find_variant": 2}),
+        ("find: no compression", {"find_variant": 3}),
+        ("union: randomised linking (Jayanti-Tarjan)", {"link_order": 1}),
+        ("sizes: per-block hash table", {"size_count": 1}),
+        ("tie rule: distance < l_x", {"tie_rule": 1}),
+    ]
+    out = []
+    clocks = _clocks_start()
+    for name, fields in variants:
+        opt = fof.fof_options()
+        for k, v in fields.items():
+            setattr(opt, k, v)
+        h = fof.fof_create_ex(box, l_x, n, opt)
+        stream = torch.cuda.Stream()
+        for _ in range(args.warmup):
+            fof.fof_link(h, pos, stream)
+            fof.fof_groups(h, ids, sizes, None, 0, 20, 1, stream)
+        fof.fof_set_timing(h, True)
+        fof.fof_reset_times(h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fof.fof_link(h, pos, stream)
+            _, ng, _ = fof.fof_groups(h, ids, sizes, None, 0, 20, 1, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ph = fof.fof_phase_times(h)
+        fof.fof_destroy(h)
+        got = ids.cpu().numpy()
+        if ref is None:
+            ref = got.copy()
+        same = bool(np.array_equal(got, ref))
+        out.append({"variant": name, "options": fields, "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                    "phases_ms": {k: v[0] / args.steps for k, v in ph.items() if v[0] > 0},
+                    "ids_equal_default": same, "n_groups": ng[0]})
+    line = {"metric": "ms per step by union-find variant", "workload": wl["name"], "n": n,
+            "steps": args.steps, "warmup": args.warmup, "variants": out, "clocks": clocks.stop()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_relink(args):
+    """fof_relink against fof_link on the same workload after the particles
+    move: unmoved (path 0), moved toward their cell centres (no cell change,
+    path 0), and displaced by a small random step (typically path 2 on a
+    large box: some particle always leaves its brick).  Device times with
+    CUDA events; ids checked equal to fof_link's."""
+    import numpy as np
+    import torch
+    from paper_2003_11468_gb300 import fof
+    fof.load()
+    wl = workloads()[args.workload]()
+    n, box, l_x = wl["n"], wl["box"], wl["l_x"]
+    pos0 = torch.from_numpy(wl["make"]()).cuda()
+    geo = fof.fof_box_geometry(box, l_x, n)
+    inv = torch.tensor(geo.inv_fine, dtype=torch.float32, device="cuda")
+    q = geo.sub_cells
+    fine = torch.clamp((pos0 * inv).to(torch.int32), max=geo.fine_per_axis - 1)
+    cell = torch.div(fine, q, rounding_mode="floor")
+    centre = ((cell.to(torch.float64) + 0.5) * q / float(geo.inv_fine)).to(torch.float32)
+    near = pos0 + 0.3 * (centre - pos0)
+    cn = torch.div(torch.clamp((near * inv).to(torch.int32), max=geo.fine_per_axis - 1), q, rounding_mode="floor")
+    keep = (cn == cell).all(dim=1, keepdim=True)
+    near = torch.where(keep, near, pos0).contiguous()
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    step = 0.01 * l_x
+    jit = torch.remainder(pos0.double() + step * torch.randn(pos0.shape, device="cuda", generator=gen,
+                                                             dtype=torch.float64), box).float()
+    jit = torch.where(jit >= float(np.float32(box)), torch.zeros_like(jit), jit).contiguous()
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    ids_ref = torch.empty_like(ids)
+    sizes = torch.empty_like(ids)
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h = fof.fof_create(box, l_x, n)
+    href = fof.fof_create(box, l_x, n)
+    res = []
+    clocks = _clocks_start()
+    for name, p in (("unmoved", pos0), ("toward cell centres", near), (f"random step {step:.3g}", jit)):
+        fof.fof_link(href, p, stream)
+        fof.fof_groups(href, ids_ref, sizes, None, 0, 20, 1, stream)
+        t_link, t_relink, paths = [], [], []
+        for _ in range(max(1, args.steps // 2)):
+            fof.fof_link(h, pos0, stream)                  # the previous binning
+            fof.fof_groups(h, ids, sizes, None, 0, 20, 1, stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fof.fof_link(h, p, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_link.append(e0.elapsed_time(e1))
+            fof.fof_link(h, pos0, stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            paths.append(fof.fof_relink(h, p, stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_relink.append(e0.elapsed_time(e1))
+            fof.fof_groups(h, ids, sizes, None, 0, 20, 1, stream)
+        res.append({"case": name, "path": paths[-1], "fof_link_ms": statistics.median(t_link),
+                    "fof_relink_ms": statistics.median(t_relink),
+                    "ids_equal": bool(torch.equal(ids, ids_ref))})
+    fof.fof_destroy(h)
+    fof.fof_destroy(href)
+    print(json.dumps({"metric": "fof_relink vs fof_link (ms, linking phase only)", "workload": wl["name"],
+                      "n": n, "cases": res, "clocks": clocks.stop()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,6 +843,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-tune", action="store_true", help="batch workload: library default options")
     ap.add_argument("--workload", default="1024", choices=["1024", "1024s", "256", "32k", "batch", "served"])
+    ap.add_argument("--ablation", action="store_true", help="time the union-find variants on --workload")
+    ap.add_argument("--relink", action="store_true", help="time fof_relink against fof_link on --workload")
     ap.add_argument("--boxes", type=int, default=512, help="batch workload: number of boxes")
     ap.add_argument("--requests", type=int, default=2000, help="served workload: requests")
     ap.add_argument("--served-repeats", type=int, default=3, help="served workload: timed repeats")
@@ -730,6 +859,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ablation:
+        return run_ablation(args)
+    if args.relink:
+        return run_relink(args)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "served":
