@@ -485,6 +485,7 @@ def batch_record(args) -> dict:
     del poss
     offs = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
     stream = torch.cuda.Stream()
+    torch.cuda.synchronize()                           # inputs written before the library's stream reads them
     boxes, lxs = [sp["box"] for sp in specs], [sp["l_x"] for sp in specs]
     # plan options picked by the autotuner on this batch (untimed; FOF_TUNE_CACHE caches them)
     opt, tuned, t_tune = None, None, 0.0
@@ -722,9 +723,11 @@ def run_ablation(args):
     n, box, l_x = wl["n"], wl["box"], wl["l_x"]
     ids = torch.empty(n, dtype=torch.int32, device="cuda")
     sizes = torch.empty_like(ids)
+    torch.cuda.synchronize()                           # inputs written before the library's stream reads them
     ref = None
     variants = [
         ("default: halving on paths of depth >= 2, hook onto the smaller root, warp-aggregated sizes", {}),
+        ("control: the default through the variant-capable kernels", {"debug_flags": 2}),
         ("find: halving at every depth", {"find_variant": 1}),
         ("find: full compression", {"find_variant": 2}),
         ("find: no compression", {"find_variant": 3}),
@@ -781,36 +784,51 @@ def run_relink(args):
     n, box, l_x = wl["n"], wl["box"], wl["l_x"]
     pos0 = torch.from_numpy(wl["make"]()).cuda()
     geo = fof.fof_box_geometry(box, l_x, n)
-    inv = torch.tensor(geo.inv_fine, dtype=torch.float32, device="cuda")
-    q = geo.sub_cells
-    fine = torch.clamp((pos0 * inv).to(torch.int32), max=geo.fine_per_axis - 1)
-    cell = torch.div(fine, q, rounding_mode="floor")
-    centre = ((cell.to(torch.float64) + 0.5) * q / float(geo.inv_fine)).to(torch.float32)
-    near = pos0 + 0.3 * (centre - pos0)
-    cn = torch.div(torch.clamp((near * inv).to(torch.int32), max=geo.fine_per_axis - 1), q, rounding_mode="floor")
-    keep = (cn == cell).all(dim=1, keepdim=True)
-    near = torch.where(keep, near, pos0).contiguous()
-    gen = torch.Generator(device="cuda").manual_seed(7)
+    q, nf, inv = geo.sub_cells, geo.fine_per_axis, float(np.float32(geo.inv_fine))
     step = 0.01 * l_x
-    jit = torch.remainder(pos0.double() + step * torch.randn(pos0.shape, device="cuda", generator=gen,
-                                                             dtype=torch.float64), box).float()
-    jit = torch.where(jit >= float(np.float32(box)), torch.zeros_like(jit), jit).contiguous()
+    boxf = float(np.float32(box))
+    gen = torch.Generator(device="cuda").manual_seed(7)
+
+    def cells(p):
+        f = torch.clamp((p * torch.tensor(inv, dtype=torch.float32, device=p.device)).to(torch.int32),
+                        max=nf - 1)
+        return torch.div(f, q, rounding_mode="floor")
+
+    def moved(kind):
+        out = torch.empty_like(pos0)
+        chunk = 1 << 25
+        for i in range(0, n, chunk):
+            p = pos0[i:i + chunk]
+            if kind == "near":
+                c = cells(p)
+                centre = ((c.to(torch.float64) + 0.5) * q / inv).to(torch.float32)
+                m = p + 0.3 * (centre - p)
+                keep = (cells(m) == c).all(dim=1, keepdim=True)
+                out[i:i + chunk] = torch.where(keep, m, p)
+            else:
+                r = torch.randn(p.shape, device="cuda", generator=gen, dtype=torch.float32)
+                m = torch.remainder(p.double() + step * r.double(), box).float()
+                out[i:i + chunk] = torch.where(m >= boxf, torch.zeros_like(m), m)
+        return out
+
     ids = torch.empty(n, dtype=torch.int32, device="cuda")
     ids_ref = torch.empty_like(ids)
     sizes = torch.empty_like(ids)
     stream = torch.cuda.Stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     h = fof.fof_create(box, l_x, n)
-    href = fof.fof_create(box, l_x, n)
+    torch.cuda.synchronize()
     res = []
     clocks = _clocks_start()
-    for name, p in (("unmoved", pos0), ("toward cell centres", near), (f"random step {step:.3g}", jit)):
-        fof.fof_link(href, p, stream)
-        fof.fof_groups(href, ids_ref, sizes, None, 0, 20, 1, stream)
+    for name, kind in (("unmoved", None), ("toward cell centres", "near"), (f"random step {step:.3g}", "jit")):
+        p = pos0 if kind is None else moved(kind)
+        torch.cuda.synchronize()                       # inputs written before the library's stream reads them
+        fof.fof_link(h, p, stream)
+        fof.fof_groups(h, ids_ref, sizes, None, 0, 20, 1, stream)
         t_link, t_relink, paths = [], [], []
+        same = True
         for _ in range(max(1, args.steps // 2)):
             fof.fof_link(h, pos0, stream)                  # the previous binning
-            fof.fof_groups(h, ids, sizes, None, 0, 20, 1, stream)
             torch.cuda.synchronize()
             e0.record(stream)
             fof.fof_link(h, p, stream)
@@ -825,12 +843,13 @@ def run_relink(args):
             torch.cuda.synchronize()
             t_relink.append(e0.elapsed_time(e1))
             fof.fof_groups(h, ids, sizes, None, 0, 20, 1, stream)
+            same &= bool(torch.equal(ids, ids_ref))
         res.append({"case": name, "path": paths[-1], "fof_link_ms": statistics.median(t_link),
-                    "fof_relink_ms": statistics.median(t_relink),
-                    "ids_equal": bool(torch.equal(ids, ids_ref))})
+                    "fof_relink_ms": statistics.median(t_relink), "ids_equal": same})
+        del p
+        torch.cuda.empty_cache()
     fof.fof_destroy(h)
-    fof.fof_destroy(href)
-    print(json.dumps({"metric": "fof_relink vs fof_link (ms, linking phase only)", "workload": wl["name"],
+    print(json.dumps({"metric": "fof_relink vs fof_link (ms, binning + linking)", "workload": wl["name"],
                       "n": n, "cases": res, "clocks": clocks.stop()}), flush=True)
     return 0
 

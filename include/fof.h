@@ -135,9 +135,12 @@ enum {
 };
 /* debug_flags */
 enum {
-    FOF_DEBUG_UNION_NO_RETRY = 1  /* every Union that must hook gives up at
-                                     once and reports FOF_ERR_TIMEOUT: a
+    FOF_DEBUG_UNION_NO_RETRY = 1, /* every Union gives up before its first
+                                     attempt and reports FOF_ERR_TIMEOUT: a
                                      deterministic test of the retry cap     */
+    FOF_DEBUG_VARIANT_KERNELS = 2 /* run the variant-capable kernels even with
+                                     the default variants (the control when
+                                     timing the variants)                    */
 };
 
 /* ---------------------------------------------------------------------- */

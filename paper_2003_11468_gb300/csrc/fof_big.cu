@@ -292,7 +292,7 @@ cudaError_t launch_big(const Geometry& g, const Work& w, int dense_min, const Uf
     if (g.total_n == 0)
         return cudaSuccess;
     const int blocks = sm_count() * 2;
-    const bool var = uf.find != 0 || uf.link != 0;
+    const bool var = uf.var != 0;
     if (pairs) {
         if (var)
             k_big_pairs<true><<<blocks, kBigThreads, 0, s>>>(g, w, dense_min, uf);

@@ -551,7 +551,7 @@ cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, const 
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
     const int blocks = sm_count() * 2;
-    const bool var = uf.find != 0 || uf.link != 0;
+    const bool var = uf.var != 0;
     if (pairs) {
         if (var)
             k_dense_pairs<true><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);

@@ -311,6 +311,7 @@ struct UfArgs {
     int find;    // 0 halving on paths of depth >= 2, 1 halving at every depth,
                  // 2 full compression, 3 none
     int link;    // 0 hook the larger root onto the smaller, 1 randomised
+    int var;     // run the variant instantiation (a variant is selected, or forced)
 };
 
 // Random priority of a root for randomised linking: the 32-bit finaliser of

@@ -787,7 +787,7 @@ cudaError_t launch_link(const Geometry& g, const Work& w, int dense_min, const U
     int64_t blocks = (warps * kWarp + kLinkThreads - 1) / kLinkThreads;
     int64_t cap = (int64_t)sm_count() * 8;
     if (blocks > cap) blocks = cap;
-    if (uf.find != 0 || uf.link != 0)
+    if (uf.var)
         k_link<true><<<(unsigned)blocks, kLinkThreads, 0, s>>>(g, w.sorted, w.cell_start, w.parent, dense_min, uf);
     else
         k_link<false><<<(unsigned)blocks, kLinkThreads, 0, s>>>(g, w.sorted, w.cell_start, w.parent, dense_min, uf);

@@ -141,7 +141,7 @@ int setup_box(double L, double l_x, int64_t n, const fof_options* o, BoxDev& b)
     if (o && (o->tie_rule < 0 || o->tie_rule > FOF_TIE_LT || o->find_variant < 0 ||
               o->find_variant > FOF_FIND_NONE || o->size_count < 0 || o->size_count > FOF_SIZE_HASH ||
               o->link_order < 0 || o->link_order > FOF_LINK_RANDOM ||
-              (o->debug_flags & ~FOF_DEBUG_UNION_NO_RETRY) != 0 || o->reserved[0] != 0 ||
+              (o->debug_flags & ~(FOF_DEBUG_UNION_NO_RETRY | FOF_DEBUG_VARIANT_KERNELS)) != 0 || o->reserved[0] != 0 ||
               o->reserved[1] != 0 || o->team_min < 0 || o->dense_min < 0 || o->retry_cap < 0))
         return FOF_ERR_ARG;
     std::memset(&b, 0, sizeof(b));
@@ -340,6 +340,7 @@ struct fof_plan {
     int find_variant = 0;
     int link_order = 0;
     int size_count = 0;
+    bool force_var = false;
     bool linked = false;
     bool binned = false;      // the binned order of the last fof_link is in place
     int last_relink_path = -1;
@@ -524,6 +525,7 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
         h->find_variant = opt->find_variant;
         h->link_order = opt->link_order;
         h->size_count = opt->size_count;
+        h->force_var = (opt->debug_flags & FOF_DEBUG_VARIANT_KERNELS) != 0;
     }
     h->rl = results_layout(nbox);
     if (workspace) {
@@ -615,6 +617,7 @@ UfArgs uf_args(const fof_plan* h)
     u.err = &h->w.status->err;
     u.find = h->find_variant;
     u.link = h->link_order;
+    u.var = (u.find != 0 || u.link != 0 || h->force_var) ? 1 : 0;
     return u;
 }
 
@@ -1339,6 +1342,7 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
         uf.err = &w.status->err;
         uf.find = 0;
         uf.link = 0;
+        uf.var = 0;
         FOF_TRY(launch_big(g, w, kDefaultDenseMin, uf, false, s));
         FOF_TRY(launch_dense(g, w, kDefaultDenseMin, uf, false, s));
         FOF_TRY(launch_dense(g, w, kDefaultDenseMin, uf, true, s));

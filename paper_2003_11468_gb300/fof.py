@@ -51,6 +51,7 @@ FOF_FIND_HALVE_DEEP, FOF_FIND_HALVE_ALL, FOF_FIND_FULL, FOF_FIND_NONE = 0, 1, 2,
 FOF_SIZE_WARP, FOF_SIZE_HASH = 0, 1
 FOF_LINK_MIN, FOF_LINK_RANDOM = 0, 1
 FOF_DEBUG_UNION_NO_RETRY = 1
+FOF_DEBUG_VARIANT_KERNELS = 2
 
 
 class fof_geometry(ctypes.Structure):
