@@ -32,7 +32,6 @@ namespace fofgpu {
 
 namespace {
 
-constexpr int kDenseThreads = 512;
 
 struct DenseSmem {
     float4* P;           // [kDenseMax] positions of the cell, slot order
@@ -50,18 +49,26 @@ struct DenseSmem {
     unsigned* rowmask;   // [kMaxQ * kMaxQ] per (z, y) row: bit x = sub-cell non-empty
 };
 
+// Two size classes of dense cells, each its own instantiation: cells up to
+// kDenseSmall particles take a quarter of the shared memory, so four CTAs
+// (of 256 threads) share an SM and barrier stalls of one cell overlap the
+// work of three others; larger cells take two CTAs of 512 threads per SM.
+constexpr int kDenseSmall = 768;
+
+template <int kM>
 __host__ __device__ constexpr size_t dense_smem_bytes()
 {
-    return (size_t)kDenseMax * (16 + 4 + 2 + 2) + (size_t)(kMaxQ3 + 1) * 4 + (size_t)kMaxQ3 * 4 +
+    return (size_t)kM * (16 + 4 + 2 + 2) + (size_t)(kMaxQ3 + 1) * 4 + (size_t)kMaxQ3 * 4 +
            (size_t)kMaxQ3 * 2 + 512 + (size_t)kMaxQ * kMaxQ * 4;
 }
 
+template <int kM>
 __device__ __forceinline__ DenseSmem carve(unsigned char* base)
 {
     DenseSmem s;
     size_t off = 0;
-    s.P = (float4*)(base + off);           off += (size_t)kDenseMax * 16;
-    s.lpar = (int*)(base + off);           off += (size_t)kDenseMax * 4;
+    s.P = (float4*)(base + off);           off += (size_t)kM * 16;
+    s.lpar = (int*)(base + off);           off += (size_t)kM * 4;
     s.sstart = (int*)(base + off);         off += (size_t)(kMaxQ3 + 1) * 4;
     s.groot = (int*)(base + off);          off += (size_t)kMaxQ3 * 4;
     s.misc = (int*)(base + off);
@@ -71,8 +78,8 @@ __device__ __forceinline__ DenseSmem carve(unsigned char* base)
     s.nbdone = s.misc + 100;
     off += 512;
     s.rowmask = (unsigned*)(base + off);   off += (size_t)kMaxQ * kMaxQ * 4;
-    s.skey = (unsigned short*)(base + off); off += (size_t)kDenseMax * 2;
-    s.order = (unsigned short*)(base + off); off += (size_t)kDenseMax * 2;
+    s.skey = (unsigned short*)(base + off); off += (size_t)kM * 2;
+    s.order = (unsigned short*)(base + off); off += (size_t)kM * 2;
     s.ne = (unsigned short*)(base + off);
     return s;
 }
@@ -279,18 +286,20 @@ __device__ __forceinline__ int neighbour_of(const DenseSmem& S, int t)
     return lo;
 }
 
-template <bool kVar>
-__global__ void __launch_bounds__(kDenseThreads, 2) k_dense_self(Geometry g, Work w, int dense_min,
+template <bool kVar, int kLo, int kM, int kThreads, int kBlocks>
+__global__ void __launch_bounds__(kThreads, kBlocks) k_dense_self(Geometry g, Work w, int dense_min,
                                                               UfArgs uf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const DenseSmem S = carve(smem_raw);
+    const DenseSmem S = carve<kM>(smem_raw);
     int* err = uf.err;
     const int n_dense = *w.n_dense;
     for (int it = blockIdx.x; it < n_dense; it += gridDim.x) {
         const int64_t key = w.dense_list[it];
         const int c0 = w.cell_start[key], c1 = w.cell_start[key + 1];
         const int m = c1 - c0;
+        if (m <= kLo || m > kM)
+            continue;                             // the other size class's cell (block-uniform)
         const BoxDev& b = g.boxes[box_of(g.box_p0, g.nbox, c0)];
         const int q = b.q;
         const float4 p0 = w.sorted[c0];
@@ -438,18 +447,20 @@ __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_self(Geometry g, Wor
     }
 }
 
-template <bool kVar>
-__global__ void __launch_bounds__(kDenseThreads, 2) k_dense_pairs(Geometry g, Work w, int dense_min,
+template <bool kVar, int kLo, int kM, int kThreads, int kBlocks>
+__global__ void __launch_bounds__(kThreads, kBlocks) k_dense_pairs(Geometry g, Work w, int dense_min,
                                                                UfArgs uf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const DenseSmem S = carve(smem_raw);
+    const DenseSmem S = carve<kM>(smem_raw);
     int* err = uf.err;
     const int n_dense = *w.n_dense;
     for (int it = blockIdx.x; it < n_dense; it += gridDim.x) {
         const int64_t key = w.dense_list[it];
         const int c0 = w.cell_start[key], c1 = w.cell_start[key + 1];
         const int m = c1 - c0;
+        if (m <= kLo || m > kM)
+            continue;                             // the other size class's cell (block-uniform)
         const BoxDev& b = g.boxes[box_of(g.box_p0, g.nbox, c0)];
         const int q = b.q;
         const float4 p0 = w.sorted[c0];
@@ -522,17 +533,29 @@ __global__ void __launch_bounds__(kDenseThreads, 2) k_dense_pairs(Geometry g, Wo
 
 size_t dense_smem()
 {
-    return dense_smem_bytes();
+    return dense_smem_bytes<kDenseMax>();
 }
 
-template <bool kVar>
+template <bool kVar, int kLo, int kM, int kThreads, int kBlocks>
 cudaError_t configure_dense()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_self<kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dense_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(k_dense_self<kVar, kLo, kM, kThreads, kBlocks>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes<kM>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_dense_pairs<kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dense_smem_bytes());
+    return cudaFuncSetAttribute(k_dense_pairs<kVar, kLo, kM, kThreads, kBlocks>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes<kM>());
+}
+
+template <bool kVar, int kLo, int kM, int kThreads, int kBlocks>
+void run_dense(const Geometry& g, const Work& w, int dense_min, const UfArgs& uf, bool pairs, cudaStream_t s)
+{
+    const int blocks = sm_count() * kBlocks;
+    if (pairs)
+        k_dense_pairs<kVar, kLo, kM, kThreads, kBlocks><<<blocks, kThreads, dense_smem_bytes<kM>(), s>>>(
+            g, w, dense_min, uf);
+    else
+        k_dense_self<kVar, kLo, kM, kThreads, kBlocks><<<blocks, kThreads, dense_smem_bytes<kM>(), s>>>(
+            g, w, dense_min, uf);
 }
 
 cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, const UfArgs& uf, bool pairs,
@@ -544,24 +567,18 @@ cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, const 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = configure_dense<false>();
-        if (e != cudaSuccess) return e;
-        e = configure_dense<true>();
-        if (e != cudaSuccess) return e;
+        if ((e = configure_dense<false, 0, kDenseSmall, 256, 4>()) != cudaSuccess) return e;
+        if ((e = configure_dense<false, kDenseSmall, kDenseMax, 512, 2>()) != cudaSuccess) return e;
+        if ((e = configure_dense<true, 0, kDenseSmall, 256, 4>()) != cudaSuccess) return e;
+        if ((e = configure_dense<true, kDenseSmall, kDenseMax, 512, 2>()) != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    const int blocks = sm_count() * 2;
-    const bool var = uf.var != 0;
-    if (pairs) {
-        if (var)
-            k_dense_pairs<true><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);
-        else
-            k_dense_pairs<false><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);
+    if (uf.var) {
+        run_dense<true, 0, kDenseSmall, 256, 4>(g, w, dense_min, uf, pairs, s);
+        run_dense<true, kDenseSmall, kDenseMax, 512, 2>(g, w, dense_min, uf, pairs, s);
     } else {
-        if (var)
-            k_dense_self<true><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);
-        else
-            k_dense_self<false><<<blocks, kDenseThreads, dense_smem_bytes(), s>>>(g, w, dense_min, uf);
+        run_dense<false, 0, kDenseSmall, 256, 4>(g, w, dense_min, uf, pairs, s);
+        run_dense<false, kDenseSmall, kDenseMax, 512, 2>(g, w, dense_min, uf, pairs, s);
     }
     return cudaGetLastError();
 }

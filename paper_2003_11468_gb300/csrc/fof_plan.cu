@@ -45,7 +45,7 @@ const char* kPhaseNames[kNumPhases] = {
     "bin_count", "scan_bricks", "bin_scatter", "brick_sort", "team_self", "big_sort", "dense_self",
     "dense_pairs", "big_pairs", "link", "finalize", "outputs", "catalogue",
 };
-const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 2, 1, 1, 1, 1, 1, 1, 2, 4};
+const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 2, 1, 2, 2, 1, 1, 1, 2, 4};
 
 constexpr int64_t kMaxTotal = 2147483646LL;   // slots and labels are int32
 constexpr int kDefaultRetryCap = 1 << 20;
