@@ -135,6 +135,35 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* smem_warp, int& 
     return warp_off + x - v;
 }
 
+// The same for 64-bit words (fields that never carry into each other).
+__device__ __forceinline__ unsigned long long block_exclusive_scan64(unsigned long long v,
+                                                                     unsigned long long* smem_warp,
+                                                                     unsigned long long& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        unsigned long long t = lane < nw ? smem_warp[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) smem_warp[lane] = t;
+    }
+    __syncthreads();
+    const unsigned long long warp_off = wid ? smem_warp[wid - 1] : 0ull;
+    total = smem_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restrict__ in, int64_t len,
                                                               int* __restrict__ part)
 {
@@ -208,12 +237,15 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
                                                              int dense_min,
                                                              int64_t* __restrict__ team_list,
                                                              int* __restrict__ n_team,
+                                                             int* __restrict__ n_team_hi,
+                                                             int64_t team_cap,
                                                              int64_t* __restrict__ big_list,
                                                              int* __restrict__ n_big)
 {
     __shared__ int hist[kMaxR3];
     __shared__ int sw[32];
-    __shared__ int list_base[3];
+    __shared__ unsigned long long sw64[32];
+    __shared__ int list_base[4];
     for (int64_t gb = blockIdx.x; gb < g.total_bricks; gb += gridDim.x) {
         const int bi = box_of(g.box_brick0, g.nbox, gb);
         const BoxDev& b = g.boxes[bi];
@@ -237,7 +269,7 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
         int ex = block_exclusive_scan(run, sw, total);
         const int ex0 = ex;
         const int64_t cbase = b.cell0 + (gb - b.brick0) * (int64_t)r3;
-        int nd = 0, nt = 0, nbg = 0;            // this thread's dense, team and big cells
+        int nd = 0, nt = 0, nth = 0, nbg = 0;   // this thread's dense, team (small, large) and big cells
         for (int c = c0; c < c0 + per && c < r3; ++c) {
             const int h = hist[c];
             cell_start[cbase + c] = s0 + ex;
@@ -246,24 +278,35 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
                 ++nbg;
             else if (is_sub(h, b, dense_min))
                 ++nd;
-            else if (h >= b.team_min && h <= kTeamSelfMax)
+            else if (h >= b.team_min && h <= kTeamSplit)
                 ++nt;
+            else if (h >= b.team_min && h <= kTeamSelfMax)
+                ++nth;
         }
         // list slots: one reservation per brick (a shared counter per cell
-        // would serialise millions of atomics on one address)
-        int nd_tot, nt_tot, nb_tot;
-        int od = block_exclusive_scan(nd, sw, nd_tot);
-        int ot = block_exclusive_scan(nt, sw, nt_tot);
-        int obg = block_exclusive_scan(nbg, sw, nb_tot);
+        // would serialise millions of atomics on one address).  The four
+        // counts (each at most kMaxR3 per brick) share one scan as 16-bit
+        // fields of a 64-bit word.
+        unsigned long long tot4;
+        const unsigned long long o4 = block_exclusive_scan64(
+            (unsigned long long)nd | ((unsigned long long)nt << 16) | ((unsigned long long)nth << 32) |
+                ((unsigned long long)nbg << 48),
+            sw64, tot4);
+        const int nd_tot = (int)(tot4 & 0xffffu), nt_tot = (int)((tot4 >> 16) & 0xffffu);
+        const int nth_tot = (int)((tot4 >> 32) & 0xffffu), nb_tot = (int)(tot4 >> 48);
+        int od = (int)(o4 & 0xffffu), ot = (int)((o4 >> 16) & 0xffffu);
+        int oth = (int)((o4 >> 32) & 0xffffu), obg = (int)(o4 >> 48);
         if (threadIdx.x == 0) {
             list_base[0] = nd_tot ? atomicAdd(n_dense, nd_tot) : 0;
             list_base[1] = nt_tot ? atomicAdd(n_team, nt_tot) : 0;
             list_base[2] = nb_tot ? atomicAdd(n_big, nb_tot) : 0;
+            list_base[3] = nth_tot ? atomicAdd(n_team_hi, nth_tot) : 0;
         }
         __syncthreads();
         od += list_base[0];
         ot += list_base[1];
         obg += list_base[2];
+        oth += list_base[3];
         ex = ex0;
         for (int c = c0; c < c0 + per && c < r3; ++c) {
             const int h = hist[c];
@@ -274,8 +317,10 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
                 big_list[obg++] = cbase + c;
             else if (is_sub(h, b, dense_min))
                 dense_list[od++] = cbase + c;
-            else if (h >= b.team_min && h <= kTeamSelfMax)
+            else if (h >= b.team_min && h <= kTeamSplit)
                 team_list[ot++] = ((int64_t)h << 32) | (uint32_t)start;
+            else if (h >= b.team_min && h <= kTeamSelfMax)
+                team_list[team_cap - 1 - oth++] = ((int64_t)h << 32) | (uint32_t)start;
         }
         __syncthreads();
         for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
@@ -411,8 +456,8 @@ cudaError_t launch_brick_sort(const Geometry& g, const Work& w, int dense_min, c
     k_brick_sort<<<(unsigned)blocks, kSortThreads, 0, s>>>(g, w.tmp, w.bstart, w.sorted, w.parent,
                                                          w.minorig, w.cnt, w.cell_start,
                                                          &w.status->err, w.dense_list, w.n_dense,
-                                                         dense_min, w.team_list, w.n_team, w.big_list,
-                                                         w.n_big);
+                                                         dense_min, w.team_list, w.n_team, w.n_team_hi,
+                                                         w.team_cap, w.big_list, w.n_big);
     return cudaGetLastError();
 }
 

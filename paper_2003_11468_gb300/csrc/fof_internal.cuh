@@ -61,6 +61,10 @@ constexpr int kDenseMax = 3072;   // particles of a dense cell (shared memory)
 // Largest team cell whose own pairs one warp links in shared memory
 // (k_team_self); larger unsplit cells link their own pairs in k_link.
 constexpr int kTeamSelfMax = 256;
+// Team cells up to kTeamSplit particles are listed from the front of the
+// team list, larger ones from its back, so each of k_team_self's two
+// instantiations walks only its own cells.
+constexpr int kTeamSplit = 128;
 // Team cells from this size on (more than one warp word) are stored in z
 // order by k_team_self, and the kernels that stream them from the cell below
 // or above read only the z-prefix or suffix that can pair; sorting the many
@@ -459,7 +463,9 @@ struct Work {
     int* n_big;          // number of entries in big_list
     int64_t* team_list;  // [team_cap] team cells (team_min..kTeamSelfMax particles, not
                          // subdivided): size << 32 | first slot
-    int* n_team;         // number of entries in team_list
+    int* n_team;         // entries at the front of team_list (cells up to kTeamSplit)
+    int* n_team_hi;      // entries at its back (cells above kTeamSplit)
+    int64_t team_cap;    // capacity of team_list
 };
 
 constexpr int kCatTile = 2048;  // labels per catalogue tile

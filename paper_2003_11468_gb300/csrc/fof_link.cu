@@ -586,9 +586,11 @@ __device__ __forceinline__ void sort_cell_z(TeamSmem<kMax>& S, int nw, int lane)
 
 template <int kMin, int kMax>
 __global__ void __launch_bounds__(kTeamWarps * 32, team_blocks<kMax>())
-    k_team_self(Geometry g, const int64_t* __restrict__ list, const int* __restrict__ n_list, float4* sorted,
-                int* __restrict__ parent, int* __restrict__ minorig, int* err)
+    k_team_self(Geometry g, const int64_t* __restrict__ list, const int* __restrict__ n_list, int64_t back,
+                float4* sorted, int* __restrict__ parent, int* __restrict__ minorig, int* err)
 {
+    // entries from the front of the list (back == 0) or from its back end
+    auto entry = [&](int i) { return back ? list[back - 1 - i] : list[i]; };
     constexpr int kTeamMax = kMax;
     constexpr int kTeamWords = kMax / 32;
     constexpr int kAdjStride = TeamSmem<kMax>::kStride;
@@ -600,10 +602,10 @@ __global__ void __launch_bounds__(kTeamWarps * 32, team_blocks<kMax>())
     // software pipeline: the next cell's positions are loaded into
     // registers while this cell is linked, and the entry after it is read
     int it = blockIdx.x * kTeamWarps + wid;
-    int64_t e = it < n ? list[it] : 0;
+    int64_t e = it < n ? entry(it) : 0;
     float4 R[kTeamWords];
     team_fetch<kMin, kMax>(R, e, sorted, lane);
-    int64_t e_next = it + stride < n ? list[it + stride] : 0;
+    int64_t e_next = it + stride < n ? entry(it + stride) : 0;
     for (; it < n; it += stride) {
         const int c0 = (int)(uint32_t)e, m = (int)(e >> 32);
         const int nw = (m + 31) >> 5;
@@ -620,7 +622,7 @@ __global__ void __launch_bounds__(kTeamWarps * 32, team_blocks<kMax>())
         e = e_next;
         if (it + stride < n)
             team_fetch<kMin, kMax>(R, e, sorted, lane);
-        e_next = it + 2 * stride < n ? list[it + 2 * stride] : 0;
+        e_next = it + 2 * stride < n ? entry(it + 2 * stride) : 0;
         if (!in_range)                         // another instantiation's cell
             continue;
         const BoxDev& b = g.boxes[box_of(g.box_p0, g.nbox, c0)];
@@ -762,20 +764,22 @@ cudaError_t launch_team_self(const Geometry& g, const Work& w, cudaStream_t s)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(k_team_self<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)team_smem_bytes<128>());
+        e = cudaFuncSetAttribute(k_team_self<0, kTeamSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)team_smem_bytes<kTeamSplit>());
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_team_self<128, kTeamSelfMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_team_self<kTeamSplit, kTeamSelfMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)team_smem_bytes<kTeamSelfMax>());
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    k_team_self<0, 128><<<sm_count() * team_blocks<128>(), kTeamWarps * 32, team_smem_bytes<128>(), s>>>(
-        g, w.team_list, w.n_team, w.sorted, w.parent, w.minorig, &w.status->err);
+    k_team_self<0, kTeamSplit><<<sm_count() * team_blocks<kTeamSplit>(), kTeamWarps * 32,
+                                 team_smem_bytes<kTeamSplit>(), s>>>(
+        g, w.team_list, w.n_team, 0, w.sorted, w.parent, w.minorig, &w.status->err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_team_self<128, kTeamSelfMax><<<sm_count() * team_blocks<kTeamSelfMax>(), kTeamWarps * 32, team_smem_bytes<kTeamSelfMax>(), s>>>(
-        g, w.team_list, w.n_team, w.sorted, w.parent, w.minorig, &w.status->err);
+    k_team_self<kTeamSplit, kTeamSelfMax><<<sm_count() * team_blocks<kTeamSelfMax>(), kTeamWarps * 32,
+                                            team_smem_bytes<kTeamSelfMax>(), s>>>(
+        g, w.team_list, w.n_team_hi, w.team_cap, w.sorted, w.parent, w.minorig, &w.status->err);
     return cudaGetLastError();
 }
 

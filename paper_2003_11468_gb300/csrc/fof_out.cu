@@ -181,11 +181,22 @@ __global__ void __launch_bounds__(256) k_outputs_bucket(Geometry g, const float4
             continue;
         int bi = box_of(g.box_p0, g.nbox, s);
         int64_t p0 = g.boxes[bi].p0;
-        int root = parent[s];
-        int label = minorig[root];
-        int o = __float_as_int(sorted[s].w);
-        bool is_label = o == label;
-        int size = is_label || root == (int)s ? cnt[root] : 0;
+        // the input index o of slot s: minorig keeps it for every non-root
+        // (the label pass only lowers roots' entries) and for singleton
+        // roots; only a root of a larger group reads it from the binned record
+        const int root = parent[s];
+        const bool root_s = root == (int)s;
+        int o, label, size;
+        if (!root_s) {
+            o = minorig[s];
+            label = minorig[root];
+            size = o == label ? cnt[root] : 0;
+        } else {
+            size = cnt[s];
+            label = minorig[s];
+            o = size == 1 ? label : __float_as_int(sorted[s].w);
+        }
+        const bool is_label = o == label;
         int64_t gidx = p0 + o;
         int chunk = (int)(gidx >> kOutChunkLog);
         unsigned peers = __match_any_sync(active, chunk);

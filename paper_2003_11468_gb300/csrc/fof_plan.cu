@@ -375,8 +375,8 @@ namespace {
 struct Layout {
     size_t boxes, p0, brick0, results, bcount, bstart, bcursor, scan_tmp, tile_cnt, tile_off,
         cell_start, tmp, sorted, parent, minorig, cnt, dense_list, n_dense, dense_root, out_cursor,
-        team_list, n_team, big_list, n_big, total;
-    int64_t scan_len, n_tiles, dense_cap;
+        team_list, n_team, n_team_hi, big_list, n_big, total;
+    int64_t scan_len, n_tiles, dense_cap, team_cap;
 };
 
 Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cells,
@@ -413,8 +413,10 @@ Layout layout(int nbox, int64_t total_n, int64_t total_bricks, int64_t total_cel
     L.n_dense = take(4);
     L.dense_root = take(4 * (size_t)(total_n / dense_min + 2));
     L.out_cursor = take(4 * (size_t)((total_n >> kOutChunkLog) + 2));
-    L.team_list = take(8 * (size_t)(total_n / kMinTeamMin + 1));
+    L.team_cap = total_n / kMinTeamMin + 1;
+    L.team_list = take(8 * (size_t)L.team_cap);
     L.n_team = take(4);
+    L.n_team_hi = take(4);
     L.big_list = take(8 * (size_t)(total_n / (kDenseMax + 1) + 1));
     L.n_big = take(4);
     L.total = off;
@@ -594,6 +596,8 @@ int create_plan(int32_t nbox, const double* box, const double* l_x, const int64_
     w.out_cursor = (int*)(ws + L.out_cursor);
     w.team_list = (int64_t*)(ws + L.team_list);
     w.n_team = (int*)(ws + L.n_team);
+    w.n_team_hi = (int*)(ws + L.n_team_hi);
+    w.team_cap = L.team_cap;
     w.big_list = (int64_t*)(ws + L.big_list);
     w.n_big = (int*)(ws + L.n_big);
 
@@ -673,6 +677,7 @@ int enqueue_link(fof_plan* h, const float* pos, cudaStream_t s)
     phase_end(h, kPhBinScatter, s);
     FOF_TRY(cudaMemsetAsync(w.n_dense, 0, 4, s));
     FOF_TRY(cudaMemsetAsync(w.n_team, 0, 4, s));
+    FOF_TRY(cudaMemsetAsync(w.n_team_hi, 0, 4, s));
     FOF_TRY(cudaMemsetAsync(w.n_big, 0, 4, s));
     phase_begin(h, kPhBrickSort, s);
     FOF_TRY(launch_brick_sort(g, w, h->dense_min, s));
@@ -826,6 +831,7 @@ int fof_relink(fof_handle h, const float* pos_dev, int32_t* path_out, void* stre
             // brick, so the per-brick cell sort runs on the new positions
             FOF_TRY(cudaMemsetAsync(w.n_dense, 0, 4, s));
             FOF_TRY(cudaMemsetAsync(w.n_team, 0, 4, s));
+            FOF_TRY(cudaMemsetAsync(w.n_team_hi, 0, 4, s));
             FOF_TRY(cudaMemsetAsync(w.n_big, 0, 4, s));
             phase_begin(h, kPhBrickSort, s);
             FOF_TRY(launch_brick_sort(g, w, h->dense_min, s));
@@ -1314,6 +1320,8 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
     w.out_cursor = (int*)(ws + L.out_cursor);
     w.team_list = (int64_t*)(ws + L.team_list);
     w.n_team = (int*)(ws + L.n_team);
+    w.n_team_hi = (int*)(ws + L.n_team_hi);
+    w.team_cap = L.team_cap;
     w.big_list = (int64_t*)(ws + L.big_list);
     w.n_big = (int*)(ws + L.n_big);
 
@@ -1334,6 +1342,7 @@ extern "C" int fof_run_noalloc(double box, double l_x, int64_t n, const float* p
         FOF_TRY(launch_scan(w.bcount, w.bstart, tb, w.scan_tmp, w.scan_tmp_len, s));
         FOF_TRY(launch_bin_scatter(pos_dev, g, w, s));
         FOF_TRY(cudaMemsetAsync(w.n_team, 0, 4, s));
+        FOF_TRY(cudaMemsetAsync(w.n_team_hi, 0, 4, s));
         FOF_TRY(cudaMemsetAsync(w.n_big, 0, 4, s));
         FOF_TRY(launch_brick_sort(g, w, kDefaultDenseMin, s));
         FOF_TRY(launch_team_self(g, w, s));
