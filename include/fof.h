@@ -358,8 +358,10 @@ int fof_merge_links(int64_t npairs, const int64_t *a, const int64_t *b, int64_t 
  *     exceeds 32 MiB are rejected with FOF_ERR_TOO_LARGE, checked before any
  *     pointer; that is about 580,000 particles at the default occupancy.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current, and later calls in
+ *     the same context reuse it; a call after the context was re-created
+ *     (cudaDeviceReset) looks it up again.  Make the first call on a device,
+ *     and the first after a reset, before any stream capture.
  *   - Every call on a device shares the one array and overwrites it (the
  *     call clears what must start at zero).  Calls whose GPU work overlaps,
  *     from several host threads or on several streams, race and give wrong

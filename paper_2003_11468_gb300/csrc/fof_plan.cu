@@ -1239,11 +1239,45 @@ constexpr int kNoallocMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 std::mutex g_noalloc_mu;
-char* g_noalloc_ptr[kNoallocMaxDevices];   // device address of the array, per device
+char* g_noalloc_ptr[kNoallocMaxDevices];                 // device address of the array, per device
+unsigned long long g_noalloc_ctx[kNoallocMaxDevices];    // id of the context it belongs to
 
-// Device address of the scratch array on the current device.  In host code
-// the array's name is only a stand-in, so the address is looked up once per
-// device with that device current.
+// The id of the calling thread's current context (driver entry points looked
+// up through the runtime, so the library does not link the driver library).
+// Context ids are unique for the life of the process: after a device reset
+// the new context has a new id.
+bool current_context_id(unsigned long long* id)
+{
+    typedef int (*GetCurrentFn)(void** ctx);
+    typedef int (*GetIdFn)(void* ctx, unsigned long long* id);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault,
+                                             &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+        cudaGetLastError();
+    }
+    void* ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx)
+        return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array for the current device.  In host code
+// the array's name is only a stand-in, so the address is looked up with
+// cudaGetSymbolAddress, with that device current, once per device and
+// context: a later call in the same context reuses it, and a call after the
+// context was re-created (cudaDeviceReset) looks it up again instead of using
+// an address of the old context.
 int noalloc_scratch(char** out)
 {
     int dev = 0;
@@ -1251,12 +1285,20 @@ int noalloc_scratch(char** out)
     if (dev < 0 || dev >= kNoallocMaxDevices)
         return FOF_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        FOF_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_ptr[dev] = (char*)p;
+    unsigned long long id = 0;
+    if (g_noalloc_ptr[dev] && current_context_id(&id) && id == g_noalloc_ctx[dev]) {
+        *out = g_noalloc_ptr[dev];
+        return FOF_OK;
     }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    FOF_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (current_context_id(&id)) {              // cache only what can be re-validated
+        g_noalloc_ptr[dev] = (char*)p;
+        g_noalloc_ctx[dev] = id;
+    } else {
+        g_noalloc_ptr[dev] = nullptr;
+    }
+    *out = (char*)p;
     return FOF_OK;
 }
 
