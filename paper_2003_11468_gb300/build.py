@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfof_gb300.so")
+# the same sources with every neighbour-candidate slot checked against its box
+# (FOF_DEBUG_CHECKS); loaded instead of LIB when FOF_LIBRARY=debug
+DEBUG_LIB = os.path.join(HERE, "libfof_gb300_debug.so")
 SOURCES = ["fof_big.cu", "fof_bin.cu", "fof_dense.cu", "fof_link.cu", "fof_merge.cu", "fof_out.cu", "fof_plan.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,22 +40,25 @@ def _deps() -> list[str]:
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OBJ_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          debug: bool = False) -> str:
+    lib = DEBUG_LIB if debug else LIB
+    if not force and up_to_date(lib):
+        return lib
+    obj_dir = OBJ_DIR + ("_debug" if debug else "")
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
-    flags = NVCC_FLAGS + ARCH + (extra or [])
+    flags = NVCC_FLAGS + ARCH + (extra or []) + (["-DFOF_DEBUG_CHECKS"] if debug else [])
 
     def compile_one(src):
-        obj = os.path.join(OBJ_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         cmd = [cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -65,17 +71,17 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else None
     print(build(force="--force" in sys.argv or extra is not None, verbose=v or extra is not None,
-                extra=extra))
+                extra=extra, debug="--debug" in sys.argv))

@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(kBigThreads) k_big_pairs(Geometry g, Work w, i
                 const int mid = (lo + hi + 1) >> 1;
                 if (S.nbpref[mid] <= t) lo = mid; else hi = mid - 1;
             }
-            const int j = S.nbj0[lo] + (t - S.nbpref[lo]);
+            int j = S.nbj0[lo] + (t - S.nbpref[lo]);
+            FOF_DCHECK_SLOT(j, b, uf.err);
             const float4 pj = w.sorted[j];
             // pj's fine coordinates relative to the cell corner, unwrapped
             const int nf = b.nf;

@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(kThreads, kBlocks) k_dense_self(Geometry g, Wo
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
             int k = neighbour_of(S, t);
             int j = S.nbj0[k] + (t - S.nbpref[k]);
+            FOF_DCHECK_SLOT(j, b, err);
             float4 pj = w.sorted[j];
             int rx, ry, rz;
             if (!rel_fine(pj, b, ox, oy, oz, rx, ry, rz))
@@ -515,6 +516,7 @@ __global__ void __launch_bounds__(kThreads, kBlocks) k_dense_pairs(Geometry g, W
             if (single && *(volatile int*)(S.nbdone + k))
                 continue;                         // the two cells are joined already
             int j = S.nbj0[k] + (t - S.nbpref[k]);
+            FOF_DCHECK_SLOT(j, b, err);
             float4 pj = w.sorted[j];
             int rx, ry, rz;
             if (!rel_fine(pj, b, ox, oy, oz, rx, ry, rz))

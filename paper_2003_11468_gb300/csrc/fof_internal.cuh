@@ -26,6 +26,24 @@ constexpr int kErrTimeout = 2;   // a union ran out of CAS retries
 constexpr int kErrInternal = 4;  // an internal consistency check failed
 constexpr int kFindCap = 1 << 26; // steps of one Find walk (a forest path is shorter)
 
+// Debug builds (FOF_DEBUG_CHECKS, libfof_gb300_debug.so) check every
+// neighbour-candidate slot a kernel computes against its box's slot range
+// before the access; a bad slot is recorded as an internal error and the
+// access goes to the box's first slot instead (never a trap).
+#ifdef FOF_DEBUG_CHECKS
+#define FOF_DCHECK_SLOT(j, b, err)                                        \
+    do {                                                                  \
+        if ((int64_t)(j) < (b).p0 || (int64_t)(j) >= (b).p0 + (b).n) {   \
+            atomicOr((err), kErrInternal);                                \
+            (j) = (int)(b).p0;                                            \
+        }                                                                 \
+    } while (0)
+#else
+#define FOF_DCHECK_SLOT(j, b, err) \
+    do {                           \
+    } while (0)
+#endif
+
 struct BoxDev {
     int64_t p0;       // first particle of the box in the concatenated arrays
     int64_t n;        // particles in the box

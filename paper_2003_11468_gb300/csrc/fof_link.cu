@@ -191,9 +191,10 @@ __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent
             const int sm = __shfl_sync(kFull, start_k, probe);
             if (k + step <= 13 && sm <= t) k += step;
         }
-        const int j = __shfl_sync(kFull, j0k, k) + (t - __shfl_sync(kFull, start_k, k));
+        int j = __shfl_sync(kFull, j0k, k) + (t - __shfl_sync(kFull, start_k, k));
         float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
         if (jv) {
+            FOF_DCHECK_SLOT(j, b, uf.err);
             q = sorted[j];
             if (filter && k < kOwnCell) {
                 int dx, dy, dz;
@@ -424,12 +425,13 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                 const int u = cb + lane;
                 const bool uv = u < C;
                 const int it = owner_lane(cstart, uv ? u : C - 1);
-                const int jj = __shfl_sync(kFull, j0, it) + (u - __shfl_sync(kFull, cstart, it));
+                int jj = __shfl_sync(kFull, j0, it) + (u - __shfl_sync(kFull, cstart, it));
                 const int oo = __shfl_sync(kFull, o, it);
                 const float4 po = shfl4(p, oo);
                 const int pbi = __shfl_sync(kFull, bi, oo);
                 if (uv) {
                     const BoxDev& b = g.boxes[pbi];
+                    FOF_DCHECK_SLOT(jj, b, uf.err);
                     if (linked(po, sorted[jj], b))
                         uunion<kVar>(parent, (int)(base + oo), jj, uf);
                 }

@@ -15,7 +15,11 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfof_gb300.so")
+# FOF_LIBRARY=debug loads the build with every neighbour-candidate slot
+# checked (bad slots reported as FOF_ERR_INTERNAL); the default is the
+# production build
+LIB_PATH = os.path.join(HERE, "libfof_gb300_debug.so" if os.environ.get("FOF_LIBRARY") == "debug"
+                        else "libfof_gb300.so")
 
 FOF_OK = 0
 FOF_ERR_ARG = 1
