@@ -467,7 +467,7 @@ struct TeamSmem {
 template <int kMax>
 constexpr int team_blocks()
 {
-    return kMax <= 128 ? 5 : 4;
+    return kMax <= 128 ? 8 : 4;
 }
 
 template <int kMax>
