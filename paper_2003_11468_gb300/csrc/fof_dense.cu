@@ -50,9 +50,9 @@ struct DenseSmem {
 };
 
 // Two size classes of dense cells, each its own instantiation: cells up to
-// kDenseSmall particles take a quarter of the shared memory, so four CTAs
-// (of 256 threads) share an SM and barrier stalls of one cell overlap the
-// work of three others; larger cells take two CTAs of 512 threads per SM.
+// kDenseSmall particles need a sixth of the shared memory, so six CTAs (of
+// 256 threads) share an SM and barrier stalls of one cell overlap the work
+// of five others; larger cells take two CTAs of 512 threads per SM.
 constexpr int kDenseSmall = 768;
 
 template <int kM>
@@ -569,17 +569,17 @@ cudaError_t launch_dense(const Geometry& g, const Work& w, int dense_min, const 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        if ((e = configure_dense<false, 0, kDenseSmall, 256, 4>()) != cudaSuccess) return e;
+        if ((e = configure_dense<false, 0, kDenseSmall, 256, 6>()) != cudaSuccess) return e;
         if ((e = configure_dense<false, kDenseSmall, kDenseMax, 512, 2>()) != cudaSuccess) return e;
-        if ((e = configure_dense<true, 0, kDenseSmall, 256, 4>()) != cudaSuccess) return e;
+        if ((e = configure_dense<true, 0, kDenseSmall, 256, 6>()) != cudaSuccess) return e;
         if ((e = configure_dense<true, kDenseSmall, kDenseMax, 512, 2>()) != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
     if (uf.var) {
-        run_dense<true, 0, kDenseSmall, 256, 4>(g, w, dense_min, uf, pairs, s);
+        run_dense<true, 0, kDenseSmall, 256, 6>(g, w, dense_min, uf, pairs, s);
         run_dense<true, kDenseSmall, kDenseMax, 512, 2>(g, w, dense_min, uf, pairs, s);
     } else {
-        run_dense<false, 0, kDenseSmall, 256, 4>(g, w, dense_min, uf, pairs, s);
+        run_dense<false, 0, kDenseSmall, 256, 6>(g, w, dense_min, uf, pairs, s);
         run_dense<false, kDenseSmall, kDenseMax, 512, 2>(g, w, dense_min, uf, pairs, s);
     }
     return cudaGetLastError();
