@@ -9,10 +9,12 @@
 //
 // Cells with at least team_min particles are linked by the warp as a
 // team: the lanes that belong to the cell keep their current root, the
-// candidates of a neighbour cell are loaded 32 at a time (coalesced float4)
-// with a snapshot of their roots, and
-//   * a chunk is skipped when all roots on both sides already agree,
-//   * a single candidate is skipped when every lane's root equals its root,
+// candidates of the neighbour cells are loaded 32 at a time (coalesced
+// float4) and filtered by the team's bounding box, the survivors are
+// gathered in shared memory, and for up to 32 of them at once their roots
+// are taken and
+//   * the whole buffer is skipped when all roots on both sides agree,
+//   * a pair is skipped when the member's root equals the candidate's,
 // which is exact because groups only ever merge: two particles whose roots
 // were once equal stay in one group.  Sparse particles search on their own.
 //
@@ -152,11 +154,77 @@ struct TeamStage {
     int croot[32];      // root snapshot of candidate b
     int cslot[32];      // slot of candidate b
     unsigned lmask[32]; // candidates of the chunk member a is linked to
+    TeamBox box;        // the team's bounding box (kept here, not in registers)
+    Cell tc;            // the team's cell
 };
 
 constexpr int kLinkThreads = 256;
 constexpr int kLinkWarps = kLinkThreads / 32;
 constexpr int kOwnCell = 13;     // stream index of a team's own cell (cells above kTeamSelfMax)
+
+// The buffered candidates S.cpos/cslot[0..c) of a team against its m
+// members: their roots; nothing more when all roots (members and
+// candidates) agree, which is exact because groups only merge; otherwise
+// the m x c pairs are tested lane-parallel (one pair per lane and step),
+// skipping pairs whose roots already agree, linked pairs set bits in the
+// member's link mask, and each member merges with the distinct candidate
+// roots it links to.
+template <bool kVar>
+__device__ __forceinline__ void team_flush(TeamStage& S, int* __restrict__ parent, const BoxDev& b, int lane,
+                                           int m, int first, int c, const UfArgs& uf)
+{
+    __syncwarp();
+    int rj = -1;
+    if (lane < c) {
+        rj = ufind<kVar>(parent, S.cslot[lane], uf);
+        S.croot[lane] = rj;
+    }
+    const int ref = S.mroot[0];
+    const int mr = lane < m ? S.mroot[lane] : ref;
+    if (__all_sync(kFull, mr == ref && (lane >= c || rj == ref)))
+        return;
+    __syncwarp();
+    // pair t2 = a * c + bb, advanced by 32 per step without a division
+    const int P = m * c;
+    int a = lane / c;
+    int bb = lane - a * c;
+    const int qa = kWarp / c, qb = kWarp - qa * c;
+    for (int t2 = lane; t2 < P; t2 += kWarp) {
+        const float4 pm = S.mpos[a];
+        const float4 qc = S.cpos[bb];
+        const int kc = __float_as_int(qc.w);
+        bool need = kc == kOwnCell ? S.cslot[bb] > first + a : ((__float_as_int(pm.w) >> kc) & 1);
+        need = need && S.mroot[a] != S.croot[bb];
+        if (need && linked(pm, qc, b))
+            atomicOr(&S.lmask[a], 1u << bb);
+        bb += qb;
+        a += qa;
+        if (bb >= c) {
+            bb -= c;
+            ++a;
+        }
+    }
+    __syncwarp();
+    if (lane < m) {
+        unsigned links = S.lmask[lane];
+        if (links) {
+            int ri = S.mroot[lane];
+            int last = -1;
+            while (links) {
+                const int u = __ffs(links) - 1;
+                links &= links - 1u;
+                const int rt = S.croot[u];
+                if (rt != ri && rt != last) {
+                    ri = uunion<kVar>(parent, ri, rt, uf);
+                    last = rt;
+                }
+            }
+            S.mroot[lane] = ri;
+            S.lmask[lane] = 0u;
+        }
+    }
+    __syncwarp();
+}
 
 // One team cell: its members (lanes lo .. lo+m-1 of the warp, contiguous
 // slots first .. first+m-1) against every particle they can reach in the
@@ -164,15 +232,11 @@ constexpr int kOwnCell = 13;     // stream index of a team's own cell (cells abo
 // Lane k < 13 holds neighbour k's first slot and count (0 when the team does
 // not reach it or the dense kernels own it); lane 13 the rest of the own
 // cell when the cell is larger than kTeamSelfMax (k_team_self links the own
-// pairs of smaller cells).  Per chunk:
-//   * candidates outside the team's bounding box + l_x are dropped;
-//   * the chunk is skipped when all roots (members and candidates) agree,
-//     which is exact because groups only merge;
-//   * the survivors are compacted into shared memory and the m x c pairs
-//     are tested lane-parallel (one pair per lane and step), skipping pairs
-//     whose roots already agree; linked pairs set bits in the member's link
-//     mask;
-//   * each member then merges with the distinct candidate roots it links to.
+// pairs of smaller cells).  Candidates outside the team's bounding box + l_x
+// are dropped; the survivors of successive chunks are gathered in shared
+// memory (most are dropped, so a team usually fills one buffer of 32) and
+// handed to team_flush when the buffer is full and at the end, so that the
+// roots, pair tests and unions of several chunks take one round.
 template <bool kVar>
 __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent,
                                           const float4* __restrict__ sorted, const BoxDev& b, int lane,
@@ -181,7 +245,10 @@ __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent
 {
     const int start_k = warp_incl(cntk, lane) - cntk;
     const int total = __shfl_sync(kFull, start_k + cntk, 31);
-    for (int cb = 0; cb < total; cb += kWarp) {
+    int nb = 0;                                 // candidates in the buffer
+    // one pass past the end of the stream flushes the rest (team_flush is
+    // inlined once)
+    for (int cb = 0; cb < total + kWarp; cb += kWarp) {
         const int t = cb + lane;
         bool jv = t < total;
         int k = 0;                              // last stream entry starting at or before t
@@ -210,61 +277,17 @@ __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent
             }
         }
         const unsigned cand = __ballot_sync(kFull, jv);
-        if (!cand)
-            continue;
-        const int rj = jv ? ufind<kVar>(parent, j, uf) : -1;
-        const int ref = S.mroot[0];
-        const int mr = lane < m ? S.mroot[lane] : ref;
-        if (__all_sync(kFull, mr == ref && (!jv || rj == ref)))
-            continue;
         const int c = __popc(cand);
+        if (nb + c > kWarp || (cb >= total && nb > 0)) {
+            team_flush<kVar>(S, parent, b, lane, m, first, nb, uf);
+            nb = 0;
+        }
         if (jv) {
-            const int r = __popc(cand & lanemask_lt());
+            const int r = nb + __popc(cand & lanemask_lt());
             S.cpos[r] = make_float4(q.x, q.y, q.z, __int_as_float(k));
-            S.croot[r] = rj;
             S.cslot[r] = j;
         }
-        __syncwarp();
-        // pair t2 = a * c + bb, advanced by 32 per step without a division
-        const int P = m * c;
-        int a = lane / c;
-        int bb = lane - a * c;
-        const int qa = kWarp / c, qb = kWarp - qa * c;
-        for (int t2 = lane; t2 < P; t2 += kWarp) {
-            const float4 pm = S.mpos[a];
-            const float4 qc = S.cpos[bb];
-            const int kc = __float_as_int(qc.w);
-            bool need = kc == kOwnCell ? S.cslot[bb] > first + a : ((__float_as_int(pm.w) >> kc) & 1);
-            need = need && S.mroot[a] != S.croot[bb];
-            if (need && linked(pm, qc, b))
-                atomicOr(&S.lmask[a], 1u << bb);
-            bb += qb;
-            a += qa;
-            if (bb >= c) {
-                bb -= c;
-                ++a;
-            }
-        }
-        __syncwarp();
-        if (lane < m) {
-            unsigned links = S.lmask[lane];
-            if (links) {
-                int ri = S.mroot[lane];
-                int last = -1;
-                while (links) {
-                    const int u = __ffs(links) - 1;
-                    links &= links - 1u;
-                    const int rt = S.croot[u];
-                    if (rt != ri && rt != last) {
-                        ri = uunion<kVar>(parent, ri, rt, uf);
-                        last = rt;
-                    }
-                }
-                S.mroot[lane] = ri;
-                S.lmask[lane] = 0u;
-            }
-        }
-        __syncwarp();
+        nb += c;
     }
 }
 
@@ -369,8 +392,12 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                 }
                 cntk = lo;
             }
+            if (lane == 0) {
+                S.box = tbx;
+                S.tc = tc;
+            }
             __syncwarp();
-            team_cell<kVar>(S, parent, sorted, b, lane, lead, m, first, tc, j0k, cntk, tbx, b.nc >= 3, uf);
+            team_cell<kVar>(S, parent, sorted, b, lane, lead, m, first, S.tc, j0k, cntk, S.box, b.nc >= 3, uf);
         }
 
         // ---- sparse particles: their (particle, cell) items, then their
