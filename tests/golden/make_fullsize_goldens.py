@@ -77,9 +77,9 @@ def _named(which):
     return record(c["name"], pos, c["box"], c["l_x"], c["min_size"], {"seed": c["seed"]})
 
 
-def write(set_name, recs):
+def write(set_name, recs, arg):
     os.makedirs(OUT, exist_ok=True)
-    doc = {"generated_by": "tests/golden/make_fullsize_goldens.py " + set_name,
+    doc = {"generated_by": "tests/golden/make_fullsize_goldens.py " + arg,
            "machine": platform.machine(), "records": recs}
     path = os.path.join(OUT, f"{set_name}.json")
     with open(path + ".tmp", "w") as f:
@@ -95,9 +95,9 @@ def main(argv):
     oracle.build()
     procs = int(os.environ.get("GOLDEN_PROCS", str(os.cpu_count() or 1)))
     if which == "small":
-        write("small", [_named("32k"), _named("256")])
+        write("small", [_named("32k"), _named("256")], which)
     elif which == "1024":
-        write("clustered_1024", [_named("1024")])
+        write("clustered_1024", [_named("1024")], which)
     elif which in ("batch", "served"):
         from paper_2003_11468_gb300 import synth
         count = len(synth.batch_512()) if which == "batch" else len(synth.served_pool())
@@ -110,7 +110,7 @@ def main(argv):
         with mp.get_context("spawn").Pool(procs) as pool:
             recs = pool.map(fn, order, chunksize=1)
         recs.sort(key=lambda r: r.get("box_index", r.get("pool_index")))
-        write("batch_512" if which == "batch" else "served_pool", recs)
+        write("batch_512" if which == "batch" else "served_pool", recs, which)
     else:
         raise SystemExit(f"unknown set {which!r}")
     return 0
