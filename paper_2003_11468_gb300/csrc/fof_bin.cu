@@ -60,7 +60,9 @@ __global__ void __launch_bounds__(256) k_bin_count(const float* __restrict__ pos
         bool ok;
         int64_t brick = brick_of(pos, i, b, rec, ok);
         bad |= !ok;
-        unsigned peers = __match_any_sync(active, brick);
+        // brick indices fit in 31 bits (checked when the plan is made); the
+        // 32-bit match is much cheaper than the 64-bit one
+        unsigned peers = __match_any_sync(active, (int)brick);
         int leader = __ffs(peers) - 1;
         if (lane == leader)
             atomicAdd(bcount + brick, __popc(peers));
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const float* __restrict__ p
         float4 rec;
         bool ok;
         int64_t brick = brick_of(pos, i, b, rec, ok);
-        unsigned peers = __match_any_sync(active, brick);
+        unsigned peers = __match_any_sync(active, (int)brick);
         int leader = __ffs(peers) - 1;
         int rank = __popc(peers & lanemask_lt());
         int off = 0;

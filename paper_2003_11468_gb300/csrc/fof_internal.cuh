@@ -301,14 +301,51 @@ __device__ __forceinline__ int uf_find(int* parent, int x, int* err)
     return x;
 }
 
+// The Finds of x and y (the same walk and halving as uf_find), with the two
+// walks interleaved: each step issues the loads of both before using
+// either, so the two chains of dependent loads overlap.
+__device__ __forceinline__ void uf_find2(int* parent, int& x, int& y, int* err)
+{
+    int px = ld_relaxed(parent + x);
+    int py = ld_relaxed(parent + y);
+    for (int step = 0; px != x || py != y; ++step) {
+        const bool wx = px != x, wy = py != y;
+        const int gx = wx ? ld_relaxed(parent + px) : px;
+        const int gy = wy ? ld_relaxed(parent + py) : py;
+        if (step >= kFindCap || (wx && gx > px) || (wy && gy > py)) {
+            atomicOr(err, kErrInternal);
+            x = px;
+            y = py;
+            return;
+        }
+        if (wx) {
+            if (gx == px) {
+                x = px;                        // px is the root
+            } else {
+                st_relaxed(parent + x, gx);
+                x = gx;
+                px = ld_relaxed(parent + x);
+            }
+        }
+        if (wy) {
+            if (gy == py) {
+                y = py;
+            } else {
+                st_relaxed(parent + y, gy);
+                y = gy;
+                py = ld_relaxed(parent + y);
+            }
+        }
+    }
+}
+
 // Union by root: hook the larger root onto the smaller with CAS, which only
 // succeeds while the larger is still a root; otherwise re-find and retry.
 // Keeps parent[x] <= x, hence no cycles.  Returns the root reached.
 __device__ __forceinline__ int uf_union(int* parent, int a, int b, int cap, int* err)
 {
     for (int it = 0; it < cap; ++it) {
-        a = uf_find(parent, a, err);
-        b = uf_find(parent, b, err);
+        uf_find2(parent, a, b, err);
         if (a == b)
             return a;
         int hi = a > b ? a : b;

@@ -448,7 +448,8 @@ int setup_batch(int32_t nbox, const double* box, const double* l_x, const int64_
         tn += b.n;
         tb += nb3;
         tc += nb3 * (int64_t)b.r * b.r * b.r;
-        if (tn > kMaxTotal)
+        // slots and brick indices are matched and scanned as int32
+        if (tn > kMaxTotal || tb > kMaxTotal)
             return FOF_ERR_ARG;
     }
     return FOF_OK;

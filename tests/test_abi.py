@@ -81,3 +81,14 @@ def test_workspace_sizing(lib):
     assert fof.fof_workspace_bytes(1.0, 0.00625, 32768, opt) > 0
     opt.brick_cells = 3
     assert fof.fof_workspace_bytes(1.0, 0.00625, 32768, opt) == 0
+
+
+def test_brick_count_limit(lib):
+    """Brick indices are matched and scanned as int32: a plan whose boxes
+    hold more than 2^31 - 2 bricks in total is an argument error."""
+    from paper_2003_11468_gb300 import fof
+    opt = fof.fof_options()
+    opt.cells_per_axis = 1024
+    opt.brick_cells = 1                     # one cell per brick: 1024^3 bricks per box
+    assert fof.fof_batch_workspace_bytes([1.0], [1e-4], [10], opt) > 0
+    assert fof.fof_batch_workspace_bytes([1.0, 1.0], [1e-4, 1e-4], [10, 10], opt) == 0
