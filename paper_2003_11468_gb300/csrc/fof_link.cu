@@ -379,18 +379,44 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
             // pass: past it, the z gap to the team alone squares above
             // bb_reach2 (the filter's sum only adds non-negative terms, and
             // the gap only grows along the z order).
-            if (lane < 9 && b.nc >= 3 && cntk >= kSortMin && cntk >= b.team_min && cntk <= kTeamSelfMax) {
+            // The prefix end is the first slot past the cut (a monotone
+            // predicate along the z order), found by a 4-ary search: the
+            // three lanes 3k, 3k+1, 3k+2 probe neighbour k's range at its
+            // quarters in one step.
+            {
+                const int gk = lane / 3, sub = lane - 3 * gk;
+                const int src = gk < 9 ? gk : 0;
+                const int jg = __shfl_sync(kFull, j0k, src), cg = __shfl_sync(kFull, cntk, src);
+                const bool act = gk < 9 && b.nc >= 3 && cg >= kSortMin && cg >= b.team_min && cg <= kTeamSelfMax;
                 const float sz = tc.cz + 1 >= b.nc ? b.Lf : 0.f;
-                int lo = 0, hi = cntk;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    const float d = __fsub_rn(__fadd_rn(sorted[j0k + mid].z, sz), tbx.hz);
-                    if (d > 0.f && __fmul_rn(d, d) > b.bb_reach2)
-                        hi = mid;
-                    else
-                        lo = mid + 1;
+                int lo = 0, hi = act ? cg : 0;
+                while (__any_sync(kFull, lo < hi)) {
+                    const int len = hi - lo;
+                    const int p0 = lo + len / 4, p1 = lo + len / 2, p2 = lo + (3 * len) / 4;
+                    bool beyond = false;
+                    if (lo < hi) {
+                        const int pr = sub == 0 ? p0 : (sub == 1 ? p1 : p2);
+                        const float d = __fsub_rn(__fadd_rn(sorted[jg + pr].z, sz), tbx.hz);
+                        beyond = d > 0.f && __fmul_rn(d, d) > b.bb_reach2;
+                    }
+                    const unsigned g3 = (__ballot_sync(kFull, beyond) >> (3 * src)) & 7u;
+                    if (lo < hi) {
+                        if (g3 & 1u) {
+                            hi = p0;
+                        } else if (g3 & 2u) {
+                            lo = p0 + 1;
+                            hi = p1;
+                        } else if (g3 & 4u) {
+                            lo = p1 + 1;
+                            hi = p2;
+                        } else {
+                            lo = p2 + 1;
+                        }
+                    }
                 }
-                cntk = lo;
+                const int cut = __shfl_sync(kFull, lo, 3 * (lane < 9 ? lane : 0));
+                if (lane < 9 && b.nc >= 3 && cntk >= kSortMin && cntk >= b.team_min && cntk <= kTeamSelfMax)
+                    cntk = cut;
             }
             if (lane == 0) {
                 S.box = tbx;
