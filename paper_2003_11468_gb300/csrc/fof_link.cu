@@ -82,6 +82,24 @@ __device__ __forceinline__ unsigned reach_mask(const float4& p, const BoxDev& b,
     return (hz ? m9 : 0u) | (hy ? xm << 9 : 0u) | (hx << 12);
 }
 
+// 16-byte asynchronous copy global -> shared (cp.async), its commit and
+// the wait for all of the thread's copies
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ float4 shfl4(float4 v, int src)
 {
     v.x = __shfl_sync(kFull, v.x, src);
@@ -297,15 +315,23 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                                                        int dense_min, UfArgs uf)
 {
     __shared__ TeamStage stage[kLinkWarps];
+    // each lane's binned record of the warp's next window, copied ahead
+    // (cp.async) while the current window is linked; two buffers
+    __shared__ float4 ahead[kLinkWarps][2][kWarp];
     const int lane = threadIdx.x & 31;
     TeamStage& S = stage[threadIdx.x >> 5];
+    float4* pf = &ahead[threadIdx.x >> 5][0][0];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     if (lane < 32)
         S.lmask[lane] = 0u;
     __syncwarp();
+    if (warp * kWarp + lane < g.total_n)
+        cp_async16(pf + lane, sorted + warp * kWarp + lane);
+    cp_async_commit();
 
-    for (int64_t base = warp * kWarp; base < g.total_n; base += nwarps * kWarp) {
+    int par = 0;
+    for (int64_t base = warp * kWarp; base < g.total_n; base += nwarps * kWarp, par ^= 1) {
         const int64_t s = base + lane;
         const bool valid = s < g.total_n;
         float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -313,8 +339,14 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
         Cell c{0, 0, 0};
         int64_t self = -1;
         int c0 = 0, c1 = 0;
+        cp_async_wait_all();                    // this lane's copy of slot s
+        if (valid)
+            p = pf[par * kWarp + lane];
+        // the other buffer was read one window ago: refill it
+        if (s + nwarps * kWarp < g.total_n)
+            cp_async16(pf + (par ^ 1) * kWarp + lane, sorted + s + nwarps * kWarp);
+        cp_async_commit();
         if (valid) {
-            p = sorted[s];
             bi = box_of(g.box_p0, g.nbox, s);
             const BoxDev& b = g.boxes[bi];
             c.cx = cell_coord(p.x, b);
