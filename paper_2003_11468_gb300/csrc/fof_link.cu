@@ -412,9 +412,12 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
             // bb_reach2 (the filter's sum only adds non-negative terms, and
             // the gap only grows along the z order).
             // The prefix end is the first slot past the cut (a monotone
-            // predicate along the z order), found by a 4-ary search: the
-            // three lanes 3k, 3k+1, 3k+2 probe neighbour k's range at its
-            // quarters in one step.
+            // predicate along the z order), bracketed by two rounds of a
+            // 4-ary search: the three lanes 3k, 3k+1, 3k+2 probe neighbour
+            // k's range at its quarters in one round.  The cut keeps [0, hi):
+            // every slot from hi on is past the cut, so it is conservative
+            // (the box filter drops the few kept slots between the first
+            // slot past the cut and hi).
             {
                 const int gk = lane / 3, sub = lane - 3 * gk;
                 const int src = gk < 9 ? gk : 0;
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                 const bool act = gk < 9 && b.nc >= 3 && cg >= kSortMin && cg >= b.team_min && cg <= kTeamSelfMax;
                 const float sz = tc.cz + 1 >= b.nc ? b.Lf : 0.f;
                 int lo = 0, hi = act ? cg : 0;
-                while (__any_sync(kFull, lo < hi)) {
+                for (int round = 0; round < 2 && __any_sync(kFull, lo < hi); ++round) {
                     const int len = hi - lo;
                     const int p0 = lo + len / 4, p1 = lo + len / 2, p2 = lo + (3 * len) / 4;
                     bool beyond = false;
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                         }
                     }
                 }
-                const int cut = __shfl_sync(kFull, lo, 3 * (lane < 9 ? lane : 0));
+                const int cut = __shfl_sync(kFull, hi, 3 * (lane < 9 ? lane : 0));   // lo <= answer <= hi
                 if (lane < 9 && b.nc >= 3 && cntk >= kSortMin && cntk >= b.team_min && cntk <= kTeamSelfMax)
                     cntk = cut;
             }
