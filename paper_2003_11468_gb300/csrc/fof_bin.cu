@@ -274,7 +274,6 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
         int nd = 0, nt = 0, nth = 0, nbg = 0;   // this thread's dense, team (small, large) and big cells
         for (int c = c0; c < c0 + per && c < r3; ++c) {
             const int h = hist[c];
-            cell_start[cbase + c] = s0 + ex;
             ex += h;
             if (is_big(h, b))
                 ++nbg;
@@ -340,8 +339,14 @@ __global__ void __launch_bounds__(kSortThreads) k_brick_sort(Geometry g, const f
             parent[k] = k;
             cnt[k] = 1;
         }
-        if (gb == g.total_bricks - 1 && threadIdx.x == 0)
-            cell_start[g.total_cells] = (int)g.total_n;
+        // the cursors now hold each cell's end: the cell starts, written
+        // coalesced (cell c + 1 starts where c ends; the next brick writes
+        // the same value at its first cell)
+        __syncthreads();
+        for (int c = threadIdx.x; c < r3; c += blockDim.x)
+            cell_start[cbase + c + 1] = s0 + hist[c];
+        if (threadIdx.x == 0)
+            cell_start[cbase] = s0;
         __syncthreads();
     }
 }

@@ -543,11 +543,20 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
 // shared memory and registers, twice the resident warps) and for 129..256.
 constexpr int kTeamWarps = 4;
 
+// Cells of up to 128 particles copy the next cell's positions ahead into
+// shared memory (cp.async, buffer Q) instead of registers.
+template <int kMax>
+constexpr bool team_ahead_smem()
+{
+    return kMax <= 128;
+}
+
 template <int kMax>
 struct TeamSmem {
     static constexpr int kWords = kMax / 32;
     static constexpr int kStride = kWords + 1;         // odd stride: conflict-free rows
     float4 P[kMax];
+    float4 Q[team_ahead_smem<kMax>() ? kMax : 1];     // the next cell, copied ahead
     unsigned adj[kMax * kStride];
 };
 
@@ -572,10 +581,11 @@ constexpr float kFar = 1e30f;
 // Tests of lane i's particle against particles jb*32 + t, t < jn8 (a
 // multiple of 8), returning row i's word of block jb.  For an off-diagonal
 // block (kOff) the ballot of each test is row j's word of block ib and is
-// stored by lane 0.  The float32 pre-test decides a group of 8 pairs in an
-// unrolled loop; pairs in the uncertainty band take the exact test after the
-// group, in a loop entered only when some lane has one, so the unrolled body
-// stays small.  Inside one cell no pair needs the periodic wrap when
+// stored by lane 0.  The float32 pre-test decides a group of 4 pairs in an
+// unrolled loop (groups of 8 hold twice the candidate registers and made
+// the 128-particle instantiation spill); pairs in the uncertainty band take
+// the exact test after the group, in a loop entered only when some lane has
+// one, so the unrolled body stays small.  Inside one cell no pair needs the periodic wrap when
 // the box has at least 3 cells per axis (the cell side is then below L/2,
 // so the wrapped float32 separation equals the plain difference); kWrap
 // takes the full predicate for boxes with fewer cells.
@@ -587,11 +597,11 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
     const float4* pj = &S.P[jb * 32];
     unsigned* colp = &S.adj[jb * 32 * kAdjStride + ib];
     unsigned row = 0;
-    for (int t0 = 0; t0 < jn8; t0 += 8) {
-        // 8 pre-tests: certainly linked (below t_lo) or undecided (the band)
+    for (int t0 = 0; t0 < jn8; t0 += 4) {
+        // 4 pre-tests: certainly linked (below t_lo) or undecided (the band)
         unsigned byte = 0, band = 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
             const float4 q = pj[t0 + u];
             float s2;
             if (kWrap) {
@@ -613,7 +623,7 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
         }
         // the exact test for the undecided pairs (rare)
         if (__any_sync(kFull, band != 0u)) {
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 const bool ex = ((band >> u) & 1u) && linked_exact_inl(pi, pj[t0 + u], b.L, b.l2);
                 byte |= (unsigned)ex << u;
                 if (kOff) {
@@ -640,6 +650,20 @@ __device__ __forceinline__ void team_fetch(float4 (&R)[kMax / 32], int64_t e, co
     for (int r = 0; r < kMax / 32; ++r)
         if (lane + 32 * r < m)
             R[r] = sorted[c0 + lane + 32 * r];
+}
+
+// The same into shared memory (S.Q) with cp.async, one commit group.
+template <int kMin, int kMax>
+__device__ __forceinline__ void team_fetch_smem(TeamSmem<kMax>& S, int64_t e, const float4* sorted, int lane)
+{
+    const int c0 = (int)(uint32_t)e, m = (int)(e >> 32);
+    if (m > kMin && m <= kMax) {
+#pragma unroll
+        for (int r = 0; r < kMax / 32; ++r)
+            if (lane + 32 * r < m)
+                cp_async16(&S.Q[lane + 32 * r], sorted + c0 + lane + 32 * r);
+    }
+    cp_async_commit();
 }
 
 // Sorts the staged cell (nw * 32 entries of S.P, sentinels after the cell's
@@ -689,29 +713,48 @@ __global__ void __launch_bounds__(kTeamWarps * 32, team_blocks<kMax>())
     TeamSmem<kMax>& S = reinterpret_cast<TeamSmem<kMax>*>(team_raw)[wid];
     const int n = *n_list;
     const int stride = gridDim.x * kTeamWarps;
-    // software pipeline: the next cell's positions are loaded into
-    // registers while this cell is linked, and the entry after it is read
+    // software pipeline: the next cell's positions are loaded while this
+    // cell is linked (into shared memory with cp.async for cells up to 128,
+    // into registers for larger ones), and the entry after it is read
     int it = blockIdx.x * kTeamWarps + wid;
     int64_t e = it < n ? entry(it) : 0;
-    float4 R[kTeamWords];
-    team_fetch<kMin, kMax>(R, e, sorted, lane);
+    constexpr bool kAhead = team_ahead_smem<kMax>();
+    float4 R[kAhead ? 1 : kTeamWords];
+    if constexpr (kAhead)
+        team_fetch_smem<kMin, kMax>(S, e, sorted, lane);
+    else
+        team_fetch<kMin, kMax>(R, e, sorted, lane);
     int64_t e_next = it + stride < n ? entry(it + stride) : 0;
     for (; it < n; it += stride) {
         const int c0 = (int)(uint32_t)e, m = (int)(e >> 32);
         const int nw = (m + 31) >> 5;
         const bool in_range = m > kMin && m <= kMax;
+        if constexpr (kAhead)
+            cp_async_wait_all();               // each lane reads back only its own copies
         if (in_range) {
 #pragma unroll
             for (int r = 0; r < kTeamWords; ++r) {   // the ragged tail links nothing
                 const int k = lane + 32 * r;
-                if (k < nw * 32)
-                    S.P[k] = k < m ? R[r] : make_float4(kFar, kFar, kFar, 0.f);
+                if (k < nw * 32) {
+                    float4 v = make_float4(kFar, kFar, kFar, 0.f);
+                    if (k < m) {
+                        if constexpr (kAhead)
+                            v = S.Q[k];
+                        else
+                            v = R[r];
+                    }
+                    S.P[k] = v;
+                }
             }
         }
         __syncwarp();
         e = e_next;
-        if (it + stride < n)
-            team_fetch<kMin, kMax>(R, e, sorted, lane);
+        if (it + stride < n) {
+            if constexpr (kAhead)
+                team_fetch_smem<kMin, kMax>(S, e, sorted, lane);
+            else
+                team_fetch<kMin, kMax>(R, e, sorted, lane);
+        }
         e_next = it + 2 * stride < n ? entry(it + 2 * stride) : 0;
         if (!in_range)                         // another instantiation's cell
             continue;
