@@ -597,9 +597,10 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
     const float4* pj = &S.P[jb * 32];
     unsigned* colp = &S.adj[jb * 32 * kAdjStride + ib];
     unsigned row = 0;
+    const float t_lo = b.t_lo, t_hi = b.t_hi;
     for (int t0 = 0; t0 < jn8; t0 += 4) {
         // 4 pre-tests: certainly linked (below t_lo) or undecided (the band)
-        unsigned byte = 0, band = 0;
+        unsigned byte = 0, hib = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const float4 q = pj[t0 + u];
@@ -612,9 +613,9 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
                 const float dz = __fsub_rn(pi.z, q.z);
                 s2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
             }
-            const bool lk = s2 < b.t_lo;
+            const bool lk = s2 < t_lo;
             byte |= (unsigned)lk << u;
-            band |= (unsigned)(!lk && s2 <= b.t_hi) << u;
+            hib |= (unsigned)(s2 <= t_hi) << u;
             if (kOff) {
                 const unsigned c = __ballot_sync(kFull, lk);
                 if (lane == 0)
@@ -622,6 +623,7 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
             }
         }
         // the exact test for the undecided pairs (rare)
+        const unsigned band = hib & ~byte;
         if (__any_sync(kFull, band != 0u)) {
             for (int u = 0; u < 4; ++u) {
                 const bool ex = ((band >> u) & 1u) && linked_exact_inl(pi, pj[t0 + u], b.L, b.l2);
