@@ -113,18 +113,6 @@ struct TeamBox {
     float lx, ly, lz, hx, hy, hz;
 };
 
-__device__ __forceinline__ float warp_min(float v)
-{
-    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
-__device__ __forceinline__ float warp_max(float v)
-{
-    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;
@@ -173,7 +161,7 @@ struct TeamStage {
     int cslot[32];      // slot of candidate b
     unsigned lmask[32]; // candidates of the chunk member a is linked to
     TeamBox box;        // the team's bounding box (kept here, not in registers)
-    Cell tc;            // the team's cell
+    float4 shift[16];   // periodic shift of stream entry k's positions (k < 13)
 };
 
 constexpr int kLinkThreads = 256;
@@ -258,7 +246,7 @@ __device__ __forceinline__ void team_flush(TeamStage& S, int* __restrict__ paren
 template <bool kVar>
 __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent,
                                           const float4* __restrict__ sorted, const BoxDev& b, int lane,
-                                          int lo, int m, int first, const Cell& tc, int j0k, int cntk,
+                                          int lo, int m, int first, int j0k, int cntk,
                                           const TeamBox& tb, bool filter, const UfArgs& uf)
 {
     const int start_k = warp_incl(cntk, lane) - cntk;
@@ -282,12 +270,8 @@ __device__ __forceinline__ void team_cell(TeamStage& S, int* __restrict__ parent
             FOF_DCHECK_SLOT(j, b, uf.err);
             q = sorted[j];
             if (filter && k < kOwnCell) {
-                int dx, dy, dz;
-                fwd_offset(k, dx, dy, dz);
-                const float sx = tc.cx + dx < 0 ? -b.Lf : (tc.cx + dx >= b.nc ? b.Lf : 0.f);
-                const float sy = tc.cy + dy < 0 ? -b.Lf : (tc.cy + dy >= b.nc ? b.Lf : 0.f);
-                const float sz = tc.cz + dz >= b.nc ? b.Lf : 0.f;
-                const float xx = q.x + sx, yy = q.y + sy, zz = q.z + sz;
+                const float4 sh = S.shift[k];
+                const float xx = q.x + sh.x, yy = q.y + sh.y, zz = q.z + sh.z;
                 const float gx = fmaxf(0.f, fmaxf(tb.lx - xx, xx - tb.hx));
                 const float gy = fmaxf(0.f, fmaxf(tb.ly - yy, yy - tb.hy));
                 const float gz = fmaxf(0.f, fmaxf(tb.lz - zz, zz - tb.hz));
@@ -374,14 +358,21 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
             tc.cx = __shfl_sync(kFull, c.cx, lead);
             tc.cy = __shfl_sync(kFull, c.cy, lead);
             tc.cz = __shfl_sync(kFull, c.cz, lead);
-            const float inf = __int_as_float(0x7f800000);
+            // coordinates are finite and >= 0 (x + 0 turns -0 into +0), so
+            // their bit patterns order like the values: one integer
+            // reduction per bound
             TeamBox tbx;
-            tbx.lx = warp_min(mine ? p.x : inf);
-            tbx.ly = warp_min(mine ? p.y : inf);
-            tbx.lz = warp_min(mine ? p.z : inf);
-            tbx.hx = warp_max(mine ? p.x : -inf);
-            tbx.hy = warp_max(mine ? p.y : -inf);
-            tbx.hz = warp_max(mine ? p.z : -inf);
+            {
+                const unsigned ux = __float_as_uint(p.x + 0.f), uy = __float_as_uint(p.y + 0.f),
+                               uz = __float_as_uint(p.z + 0.f);
+                const unsigned hi = 0x7f800000u;  // +inf: ignored by the minimum
+                tbx.lx = __uint_as_float(__reduce_min_sync(kFull, mine ? ux : hi));
+                tbx.ly = __uint_as_float(__reduce_min_sync(kFull, mine ? uy : hi));
+                tbx.lz = __uint_as_float(__reduce_min_sync(kFull, mine ? uz : hi));
+                tbx.hx = __uint_as_float(__reduce_max_sync(kFull, mine ? ux : 0u));
+                tbx.hy = __uint_as_float(__reduce_max_sync(kFull, mine ? uy : 0u));
+                tbx.hz = __uint_as_float(__reduce_max_sync(kFull, mine ? uz : 0u));
+            }
             const unsigned reach = mine ? reach_mask(p, b, tc) : 0u;
             const unsigned team_reach = __reduce_or_sync(kFull, reach);
             if (mine) {
@@ -405,6 +396,13 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
             } else if (lane == kOwnCell && cell_size > kTeamSelfMax) {
                 j0k = first + 1;
                 cntk = cell_end - first - 1;
+            }
+            if (lane < 13) {
+                int dx, dy, dz;
+                fwd_offset(lane, dx, dy, dz);
+                S.shift[lane] = make_float4(tc.cx + dx < 0 ? -b.Lf : (tc.cx + dx >= b.nc ? b.Lf : 0.f),
+                                            tc.cy + dy < 0 ? -b.Lf : (tc.cy + dy >= b.nc ? b.Lf : 0.f),
+                                            tc.cz + dz >= b.nc ? b.Lf : 0.f, 0.f);
             }
             // Neighbours k < 9 lie one cell up in z.  A team cell there (sorted
             // by z in k_team_self) is cut to the prefix that the box filter can
@@ -453,12 +451,10 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                 if (lane < 9 && b.nc >= 3 && cntk >= kSortMin && cntk >= b.team_min && cntk <= kTeamSelfMax)
                     cntk = cut;
             }
-            if (lane == 0) {
+            if (lane == 0)
                 S.box = tbx;
-                S.tc = tc;
-            }
             __syncwarp();
-            team_cell<kVar>(S, parent, sorted, b, lane, lead, m, first, S.tc, j0k, cntk, S.box, b.nc >= 3, uf);
+            team_cell<kVar>(S, parent, sorted, b, lane, lead, m, first, j0k, cntk, S.box, b.nc >= 3, uf);
         }
 
         // ---- sparse particles: their (particle, cell) items, then their
