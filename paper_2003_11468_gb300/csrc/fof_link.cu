@@ -36,6 +36,23 @@ struct Cell {
     int cx, cy, cz;
 };
 
+// cell_key with the Morton spreading of the in-brick coordinates (< 16)
+// read from a shared-memory table instead of computed
+__device__ __forceinline__ int64_t cell_key_tab(const BoxDev& b, int cx, int cy, int cz, const uint32_t* tab)
+{
+    const int m = b.r - 1;
+    const int64_t r3 = (int64_t)b.r * b.r * b.r;
+    return b.cell0 + brick_local(b, cx, cy, cz) * r3 + (tab[cx & m] | (tab[cy & m] << 1) | (tab[cz & m] << 2));
+}
+
+__device__ __forceinline__ int64_t nbr_key_tab(const BoxDev& b, const Cell& c, int k, const uint32_t* tab)
+{
+    int dx, dy, dz;
+    fwd_offset(k, dx, dy, dz);
+    return cell_key_tab(b, wrap_cell(c.cx + dx, b.nc), wrap_cell(c.cy + dy, b.nc), wrap_cell(c.cz + dz, b.nc),
+                        tab);
+}
+
 __device__ __forceinline__ int64_t nbr_key(const BoxDev& b, const Cell& c, int k)
 {
     int dx, dy, dz;
@@ -299,6 +316,10 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                                                        int dense_min, UfArgs uf)
 {
     __shared__ TeamStage stage[kLinkWarps];
+    __shared__ uint32_t spread_tab[16];
+    if (threadIdx.x < 16)
+        spread_tab[threadIdx.x] = spread3(threadIdx.x);
+    __syncthreads();
     // each lane's binned record of the warp's next window, copied ahead
     // (cp.async) while the current window is linked; two buffers
     __shared__ float4 ahead[kLinkWarps][2][kWarp];
@@ -336,7 +357,7 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
             c.cx = cell_coord(p.x, b);
             c.cy = cell_coord(p.y, b);
             c.cz = cell_coord(p.z, b);
-            self = cell_key(b, c.cx, c.cy, c.cz);
+            self = cell_key_tab(b, c.cx, c.cy, c.cz, spread_tab);
             c0 = cell_start[self];
             c1 = cell_start[self + 1];
         }
@@ -387,7 +408,7 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
             // particles after the first member, for cells k_team_self skips
             int j0k = 0, cntk = 0;
             if (lane < 13 && ((team_reach >> lane) & 1u) && !nbr_duplicate(b, tc, lane, key)) {
-                const int64_t nk = nbr_key(b, tc, lane);
+                const int64_t nk = nbr_key_tab(b, tc, lane, spread_tab);
                 const int j0 = cell_start[nk], j1 = cell_start[nk + 1];
                 if (j1 > j0 && !is_sub(j1 - j0, b, dense_min)) {
                     j0k = j0;
@@ -495,7 +516,7 @@ __global__ void __launch_bounds__(kLinkThreads) k_link(Geometry g, const float4*
                 } else {
                     const BoxDev& b = g.boxes[obi];
                     const int k = nth_bit(reach_o, r - (own_o > 0));
-                    const int64_t nk = nbr_key(b, oc, k);
+                    const int64_t nk = nbr_key_tab(b, oc, k, spread_tab);
                     const int a0 = cell_start[nk], a1 = cell_start[nk + 1];
                     if (!is_sub(a1 - a0, b, dense_min)) {
                         j0 = a0;
