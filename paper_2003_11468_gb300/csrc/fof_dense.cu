@@ -211,8 +211,12 @@ __device__ __forceinline__ int link_window(const DenseSmem& S, int* parent, cons
     for (int z = z0; z <= z1; ++z) {
         // gap from pj to the sub-cell layer z, in fine units (0 when adjacent)
         float gz = z < rz ? (float)(rz - z - 1) + uz : (z > rz ? (float)(z - rz - 1) + (1.f - uz) : 0.f);
+        if (gz * gz > b.reach2)
+            continue;                            // the whole layer is out of reach
         for (int y = y0; y <= y1; ++y) {
             float gy = y < ry ? (float)(ry - y - 1) + uy : (y > ry ? (float)(y - ry - 1) + (1.f - uy) : 0.f);
+            if (gy * gy + gz * gz > b.reach2)
+                continue;                        // the whole row is out of reach
             unsigned bits = S.rowmask[z * q + y] & span;     // non-empty sub-cells only
             while (bits) {
                 const int x = __ffs(bits) - 1;
