@@ -85,7 +85,7 @@ typedef struct {
 typedef struct {
     int32_t cells_per_axis;  /* cells per box side; must keep side >= l_x   */
     int32_t brick_cells;     /* cells per brick side: 1, 2, 4, 8 or 16      */
-    double occupancy;        /* target mean particles per cell (default 0.35) */
+    double occupancy;        /* target mean particles per cell (default 0.30) */
     int32_t dense_min;       /* cell occupancy from which a cell is split
                                 into sub-cells and linked in shared memory
                                 (default 256)                                */

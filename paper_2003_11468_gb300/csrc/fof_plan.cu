@@ -50,7 +50,7 @@ const int kPhaseLaunches[kNumPhases] = {1, 3, 1, 1, 2, 1, 2, 2, 1, 1, 1, 2, 4};
 constexpr int64_t kMaxTotal = 2147483646LL;   // slots and labels are int32
 constexpr int kDefaultRetryCap = 1 << 20;
 constexpr int kDefaultDenseMin = 256;
-constexpr double kDefaultOccupancy = 0.35;
+constexpr double kDefaultOccupancy = 0.30;
 constexpr int kDefaultTeamMin = 8;
 constexpr int kMinTeamMin = 2;                 // smallest accepted team threshold (sizes team_list)
 constexpr int kMaxCellsPerAxis = 4096;        // float32 cell-index precision (unsplit cells)
