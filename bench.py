@@ -72,8 +72,11 @@ def workloads():
     return {
         "1024": synth.clustered_1024,
         # 1/64 of the 1024^3 box at the same density, blob recipe and l_x:
-        # the small case the per-kernel ncu captures run on
-        "1024s": lambda: synth.clustered_sample_of_1024(4),
+        # the small case the per-kernel ncu captures run on; its grid is
+        # fixed at 384^3 cells (3.33 l_x wide, 6 sub-cells per axis) to match
+        # the 1024^3 box's 1520^3 (3.37 l_x, 6 sub-cells), where the default
+        # choice for the smaller box would round down to 352^3 (3.64 l_x)
+        "1024s": lambda: dict(synth.clustered_sample_of_1024(4), cells_per_axis=384),
         "256": synth.clustered_256,
         "32k": synth.uniform_32k,
     }
@@ -328,7 +331,12 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize(dev)
 
-    h = fof.fof_create(box, l_x, n)
+    if "cells_per_axis" in wl:
+        opt = fof.fof_options()
+        opt.cells_per_axis = wl["cells_per_axis"]
+        h = fof.fof_create_ex(box, l_x, n, opt)
+    else:
+        h = fof.fof_create(box, l_x, n)
     nc, r, nb = fof.fof_plan_info(h)
     cells = (nc ** 3)
 
