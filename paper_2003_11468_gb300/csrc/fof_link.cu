@@ -597,8 +597,8 @@ constexpr float kFar = 1e30f;
 
 // Tests of lane i's particle against particles jb*32 + t, t < jn8 (a
 // multiple of 8), returning row i's word of block jb.  For an off-diagonal
-// block (kOff) the ballot of each test is row j's word of block ib and is
-// stored by lane 0.  The float32 pre-test decides a group of 4 pairs in an
+// block (kOff) the ballot of each test is row j's word of block ib; lane j
+// keeps it and stores it once at the end.  The float32 pre-test decides a group of 4 pairs in an
 // unrolled loop (groups of 8 hold twice the candidate registers and made
 // the 128-particle instantiation spill); pairs in the uncertainty band take
 // the exact test after the group, in a loop entered only when some lane has
@@ -612,8 +612,8 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
 {
     constexpr int kAdjStride = TeamSmem<kMax>::kStride;
     const float4* pj = &S.P[jb * 32];
-    unsigned* colp = &S.adj[jb * 32 * kAdjStride + ib];
     unsigned row = 0;
+    unsigned col = 0;                          // off-diagonal: row (jb*32 + lane)'s word ib
     const float t_lo = b.t_lo, t_hi = b.t_hi;
     for (int t0 = 0; t0 < jn8; t0 += 4) {
         // 4 pre-tests: certainly linked (below t_lo) or undecided (the band)
@@ -635,8 +635,7 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
             hib |= (unsigned)(s2 <= t_hi) << u;
             if (kOff) {
                 const unsigned c = __ballot_sync(kFull, lk);
-                if (lane == 0)
-                    colp[(t0 + u) * kAdjStride] = c;
+                col = lane == t0 + u ? c : col;
             }
         }
         // the exact test for the undecided pairs (rare)
@@ -647,13 +646,16 @@ __device__ __forceinline__ unsigned block_tests(const float4& pi, TeamSmem<kMax>
                 byte |= (unsigned)ex << u;
                 if (kOff) {
                     const unsigned c = __ballot_sync(kFull, ex);
-                    if (c && lane == 0)
-                        colp[(t0 + u) * kAdjStride] |= c;
+                    col |= lane == t0 + u ? c : 0u;
                 }
             }
         }
         row |= byte << t0;
     }
+    // the mirrored words, one store per lane (rows past the block's
+    // particles are never read)
+    if (kOff)
+        S.adj[(jb * 32 + lane) * kAdjStride + ib] = col;
     return row;
 }
 
