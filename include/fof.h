@@ -91,7 +91,7 @@ typedef struct {
                                 (default 256)                                */
     int32_t retry_cap;       /* max CAS attempts per union (default 2^20)    */
     int32_t team_min;        /* cell occupancy from which one warp links the
-                                cell's particles as a team (default 8, >= 2) */
+                                cell's particles as a team (default 10, >= 2) */
     int32_t tie_rule;        /* FOF_TIE_LE (0, default): linked iff the
                                 distance is <= l_x (graph definition, Sec. 1
                                 footnote; "at most", abstract); FOF_TIE_LT:

@@ -86,9 +86,9 @@ constexpr int kTeamSplit = 128;
 // Team cells from this size on are stored in z order by k_team_self, and the
 // kernels that stream them from the cell below read only the z-prefix that
 // can pair; sorting the many smaller cells costs more than it saves (measured
-// on the 1024^3 box: from 17 on the cut saves 2.3 ms of linking for 1.1 ms of
-// sorting; from 9 on it saves 3.0 ms for 3.2 ms).
-constexpr int kSortMin = 17;
+// on the 1024^3 box at 0.30 particles per cell: from 25 on, together with a
+// team threshold of 10, the step is 1.5 ms shorter than from 17 with 8).
+constexpr int kSortMin = 25;
 constexpr int kMaxQ = 12;
 constexpr int kMaxQ3 = kMaxQ * kMaxQ * kMaxQ;
 

@@ -51,7 +51,7 @@ constexpr int64_t kMaxTotal = 2147483646LL;   // slots and labels are int32
 constexpr int kDefaultRetryCap = 1 << 20;
 constexpr int kDefaultDenseMin = 256;
 constexpr double kDefaultOccupancy = 0.30;
-constexpr int kDefaultTeamMin = 8;
+constexpr int kDefaultTeamMin = 10;
 constexpr int kMinTeamMin = 2;                 // smallest accepted team threshold (sizes team_list)
 constexpr int kMaxCellsPerAxis = 4096;        // float32 cell-index precision (unsplit cells)
 constexpr int kMaxFinePerAxis = 16384;        // float32 index precision (sub-cells)

@@ -29,7 +29,7 @@ from . import fof
 DEFAULT_GRID = {
     "occupancy": (0.25, 0.35, 0.5),
     "dense_min": (192, 256, 384),
-    "team_min": (4, 8),
+    "team_min": (4, 8, 10),
 }
 
 

@@ -11,7 +11,7 @@ from paper_2003_11468_gb300 import tune
 
 def test_candidate_grid_and_options():
     c = tune.candidates()
-    assert len(c) == 3 * 3 * 2
+    assert len(c) == 3 * 3 * 3
     assert len({json.dumps(x, sort_keys=True) for x in c}) == len(c)
     o = tune.options_from({"occupancy": 0.25, "dense_min": 192, "team_min": 6, "brick_cells": 8})
     assert (o.occupancy, o.dense_min, o.team_min, o.brick_cells) == (0.25, 192, 6, 8)
